@@ -1,0 +1,173 @@
+"""FP64 CPU oracle for overlap-and-save convolution -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package.  The product library
+(``paper_1910_01972_gb300``) never imports it and never falls back to it.
+
+The arithmetic lives in ``ols_oracle.c`` (plain C, FP64, OpenMP over output
+elements): the valid part of Eq. 1 for a bank of filters (Sec. 3.2 states
+that OLS returns exactly this, whatever the segment length), and the adjoint
+of that linear map.  This module only compiles the C file and marshals numpy
+arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ols_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libols_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``ols_oracle.c`` into ``libols_oracle.so`` beside it.
+
+    ``-ffp-contract=off`` keeps every multiply and add separately rounded so
+    x86 and Arm hosts give identical results; no fast-math.
+    """
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        i64, i32 = ctypes.c_int64, ctypes.c_int32
+        vp = ctypes.c_void_p
+        lib.ols_oracle_conv.argtypes = [i64, vp, i32, i32, vp, vp]
+        lib.ols_oracle_conv.restype = ctypes.c_int
+        lib.ols_oracle_conv_at.argtypes = [i64, vp, i32, i32, vp, i64, vp, vp, vp]
+        lib.ols_oracle_conv_at.restype = ctypes.c_int
+        lib.ols_oracle_adjoint.argtypes = [i64, vp, i32, i32, vp, vp, vp, vp]
+        lib.ols_oracle_adjoint.restype = ctypes.c_int
+        lib.ols_oracle_threads.argtypes = []
+        lib.ols_oracle_threads.restype = ctypes.c_int
+        lib.ols_oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.ols_oracle_set_threads.restype = None
+        _lib = lib
+        return lib
+
+
+def _c64(a) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.complex64:
+        raise TypeError("oracle inputs are complex64 (the FP32 values the GPU consumes), got %s" % a.dtype)
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_load().ols_oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().ols_oracle_set_threads(int(n))
+
+
+def conv(s, h) -> np.ndarray:
+    """Valid-mode convolution y[F][Ns-M+1] (complex128) of s[Ns] with h[F][M].
+
+    ``h`` may be 1-D (one filter), giving y of shape [Ns-M+1].
+    """
+    s = _c64(s)
+    h = _c64(h)
+    squeeze = h.ndim == 1
+    if squeeze:
+        h = h[None, :]
+    F, M = h.shape
+    Ns = s.shape[0]
+    if M < 1 or F < 1 or Ns < M:
+        raise ValueError("need M >= 1, F >= 1, Ns >= M")
+    y = np.empty((F, Ns - M + 1), dtype=np.complex128)
+    rc = _load().ols_oracle_conv(Ns, _ptr(s), M, F, _ptr(h), _ptr(y))
+    if rc != 0:
+        raise ValueError("ols_oracle_conv rejected the sizes")
+    return y[0] if squeeze else y
+
+
+def conv_at(s, h, f_idx, j_idx) -> np.ndarray:
+    """y_{f_idx[i]}[j_idx[i]] for each i (complex128)."""
+    s = _c64(s)
+    h = _c64(h)
+    if h.ndim == 1:
+        h = h[None, :]
+    F, M = h.shape
+    fi = np.ascontiguousarray(f_idx, dtype=np.int64)
+    ji = np.ascontiguousarray(j_idx, dtype=np.int64)
+    if fi.shape != ji.shape:
+        raise ValueError("index arrays differ in shape")
+    out = np.empty(fi.shape, dtype=np.complex128)
+    rc = _load().ols_oracle_conv_at(s.shape[0], _ptr(s), M, F, _ptr(h), fi.size,
+                                    _ptr(fi), _ptr(ji), _ptr(out))
+    if rc != 0:
+        raise ValueError("ols_oracle_conv_at rejected the sizes or an index")
+    return out
+
+
+def adjoint(s, h, g, want_ds: bool = True, want_dh: bool = True):
+    """Adjoint of ``conv``: returns (ds[Ns], dh[F][M]) as complex128.
+
+    ``g`` is dL/dRe y + i dL/dIm y, shape [F][Ns-M+1]; it is widened to
+    complex128 (exact for complex64 input).
+    """
+    s = _c64(s)
+    h = _c64(h)
+    g = np.ascontiguousarray(g, dtype=np.complex128)
+    squeeze = h.ndim == 1
+    if squeeze:
+        h = h[None, :]
+        g = g[None, :]
+    F, M = h.shape
+    Ns = s.shape[0]
+    if g.shape != (F, Ns - M + 1):
+        raise ValueError("g must have shape [F][Ns-M+1]")
+    ds = np.empty(Ns, dtype=np.complex128) if want_ds else None
+    dh = np.empty((F, M), dtype=np.complex128) if want_dh else None
+    rc = _load().ols_oracle_adjoint(Ns, _ptr(s), M, F, _ptr(h), _ptr(g),
+                                    _ptr(ds) if ds is not None else None,
+                                    _ptr(dh) if dh is not None else None)
+    if rc != 0:
+        raise ValueError("ols_oracle_adjoint rejected the sizes")
+    if squeeze and dh is not None:
+        dh = dh[0]
+    return ds, dh
+
+
+def rel_l2(y, y_ref) -> float:
+    """||y - y_ref||_2 / ||y_ref||_2 (in FP64)."""
+    y = np.asarray(y, dtype=np.complex128)
+    y_ref = np.asarray(y_ref, dtype=np.complex128)
+    den = np.linalg.norm(y_ref.ravel())
+    num = np.linalg.norm((y - y_ref).ravel())
+    return float(num / den) if den > 0 else float(num)
+
+
+def max_stream_rel_l2(y, y_ref) -> float:
+    """Largest per-stream relative L2 error over the leading (filter) axis."""
+    y = np.asarray(y)
+    y_ref = np.asarray(y_ref)
+    if y.ndim == 1:
+        return rel_l2(y, y_ref)
+    return max(rel_l2(y[f], y_ref[f]) for f in range(y.shape[0]))

@@ -1,0 +1,251 @@
+"""Checks that pin the FP64 oracle to facts fixed by the paper and by
+mathematics, independent of the oracle's own code.
+
+Each ``pin_*`` function takes the two oracle entry points as callables
+(``conv(s, h) -> y`` and ``adjoint(s, h, g) -> (ds, dh)``) and raises
+AssertionError on a mismatch, so the same checks run against the real oracle
+(tests/test_oracle_pins.py) and against deliberately broken copies of it
+(the mutation test), proving that each plausible mistake is caught.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ----------------------------------------------------------------- fixtures
+def read_golden(name):
+    """Parse a tests/golden/*.txt fixture into a list of dicts of arrays."""
+    cases, cur = [], {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                if not line and cur:
+                    cases.append(cur)
+                    cur = {}
+                continue
+            key, val = (x.strip() for x in line.split("=", 1))
+            if key == "case":
+                cur["case"] = val
+            else:
+                cur[key] = np.array([complex(v) for v in val.split()], dtype=np.complex128)
+    if cur:
+        cases.append(cur)
+    return cases
+
+
+def _c64(x):
+    return np.asarray(x, dtype=np.complex64)
+
+
+def naive_dft_matrix(P):
+    """Explicit P x P DFT matrix exp(-2 pi i n k / P), index product reduced mod P."""
+    n = np.arange(P)
+    e = (np.outer(n, n) % P).astype(np.float64)
+    return np.exp(-2j * math.pi * e / P)
+
+
+def quantized(g, shape, step):
+    """Complex values on a grid of ``step`` in [-1, 1] (exact in FP32)."""
+    q = np.round(g.uniform(-1, 1, size=shape) / step) * step
+    r = np.round(g.uniform(-1, 1, size=shape) / step) * step
+    return (q + 1j * r).astype(np.complex64)
+
+
+# ----------------------------------------------------------------- pins
+def pin_golden_conv(conv, adjoint=None):
+    """Hand-worked cases of Eq. 1 (tests/golden/hand_conv.txt): exact."""
+    for c in read_golden("hand_conv.txt"):
+        y = conv(_c64(c["s"]), _c64(c["h"]))
+        assert np.array_equal(y, c["y"]), (c["case"], y, c["y"])
+
+
+def pin_golden_adjoint(conv, adjoint):
+    """Hand-worked adjoint cases (tests/golden/hand_adjoint.txt): exact."""
+    for c in read_golden("hand_adjoint.txt"):
+        ds, dh = adjoint(_c64(c["s"]), _c64(c["h"]), c["g"])
+        assert np.array_equal(ds, c["ds"]), (c["case"], ds, c["ds"])
+        assert np.array_equal(np.ravel(dh), c["dh"]), (c["case"], dh, c["dh"])
+
+
+def pin_bruteforce_dft(conv, adjoint=None, seed=11):
+    """Linear convolution equals circular convolution once both operands are
+    zero-padded to P >= Ns + M - 1 (Sec. 1, Eq. 2 and its padding rule); the
+    circular convolution is evaluated with explicit O(P^2) DFT matrices.  The
+    valid outputs are entries M-1 .. Ns-1 of the full linear result."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    for Ns in (1, 2, 3, 5, 8, 17, 31, 64):
+        for M in (1, 2, 3, 4, 7, 16):
+            if M > Ns:
+                continue
+            F = 1 + (Ns + M) % 3
+            s = _c64(g.normal(size=Ns) + 1j * g.normal(size=Ns))
+            h = _c64(g.normal(size=(F, M)) + 1j * g.normal(size=(F, M)))
+            P = Ns + M - 1
+            W = naive_dft_matrix(P)
+            Winv = np.conj(W) / P
+            sp = np.zeros(P, np.complex128)
+            sp[:Ns] = s
+            S = W @ sp
+            y = conv(s, h)
+            assert y.shape == (F, Ns - M + 1)
+            for f in range(F):
+                hp = np.zeros(P, np.complex128)
+                hp[:M] = h[f]
+                full = Winv @ (S * (W @ hp))
+                ref = full[M - 1:Ns]
+                err = np.max(np.abs(y[f] - ref)) / max(1.0, np.max(np.abs(ref)))
+                assert err < 1e-13, (Ns, M, f, err)
+
+
+def pin_fft_fullconv(conv, adjoint=None, seed=12):
+    """Full-length zero-padded FFT convolution (Sec. 1: padding to at least
+    Ns + M - 1 makes the circular result linear), via numpy's FFT."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    for (Ns, M, F) in ((4096, 64, 1), (4096, 129, 3), (4096, 257, 2)):
+        s = _c64(g.uniform(-1, 1, Ns) + 1j * g.uniform(-1, 1, Ns))
+        h = _c64(g.normal(size=(F, M)) + 1j * g.normal(size=(F, M)))
+        P = 1 << int(math.ceil(math.log2(Ns + M - 1)))
+        S = np.fft.fft(s.astype(np.complex128), P)
+        y = conv(s, h)
+        for f in range(F):
+            full = np.fft.ifft(S * np.fft.fft(h[f].astype(np.complex128), P))
+            ref = full[M - 1:Ns]
+            err = np.linalg.norm(y[f] - ref) / np.linalg.norm(ref)
+            assert err < 1e-12, (Ns, M, f, err)
+
+
+def pin_delta_shift(conv, adjoint=None, seed=13):
+    """h = e_d (unit tap at d) gives y[j] = s[j + M - 1 - d], exactly."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    n = np.arange(300)
+    s_int = _c64((n % 1024) + 1j * ((7 * n) % 1024))
+    s_rand = _c64(g.uniform(-1, 1, 300) + 1j * g.uniform(-1, 1, 300))
+    for s in (s_int, s_rand):
+        for M in (1, 2, 5, 64):
+            for d in sorted({0, M // 2, M - 1}):
+                h = np.zeros(M, np.complex64)
+                h[d] = 1
+                y = conv(s, h)
+                ref = s[M - 1 - d: len(s) - d].astype(np.complex128)
+                assert np.array_equal(y, ref), (M, d)
+
+
+def pin_linearity(conv, adjoint=None, seed=14):
+    """Convolution is linear in s and in h; a bank of filters is the stack of
+    the single-filter results.  Inputs sit on a 2^-8 grid so the scaled sums
+    are exact in FP32."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    Ns, M = 200, 9
+    s1, s2 = quantized(g, Ns, 2.0 ** -8), quantized(g, Ns, 2.0 ** -8)
+    h1, h2 = quantized(g, M, 2.0 ** -8), quantized(g, M, 2.0 ** -8)
+    a, b = 2.0, -0.5
+    lhs = conv(_c64(a * s1.astype(np.complex128) + b * s2), h1)
+    rhs = a * conv(s1, h1) + b * conv(s2, h1)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-13 * np.max(np.abs(rhs))
+    lhs = conv(s1, _c64(a * h1.astype(np.complex128) + b * h2))
+    rhs = a * conv(s1, h1) + b * conv(s1, h2)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-13 * np.max(np.abs(rhs))
+    bank = conv(s1, np.stack([h1, h2]))
+    assert np.array_equal(bank[0], conv(s1, h1)) and np.array_equal(bank[1], conv(s1, h2))
+
+
+def pin_closed_forms(conv, adjoint=None, seed=15):
+    """Complex exponentials are eigenfunctions: s[n] = z^n with |z| = 1 gives
+    y[j] = z^(j+M-1) * sum_k h[k] z^(-k).  z = i and z = -1 are exact in FP32;
+    z = 1 (a constant signal) gives sum_k h[k] everywhere."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    Ns, M = 257, 13
+    h = _c64(g.normal(size=M) + 1j * g.normal(size=M))
+    hd = h.astype(np.complex128)
+    n = np.arange(Ns)
+    for z, pw in ((1j, lambda e: 1j ** (e % 4)), (-1.0, lambda e: (-1.0) ** (e % 2)),
+                  (1.0, lambda e: np.ones_like(e, dtype=np.float64))):
+        s = _c64(pw(n))
+        Hz = sum(hd[k] * np.conj(pw(np.array(k))) for k in range(M))
+        j = np.arange(Ns - M + 1)
+        ref = pw(j + M - 1) * Hz
+        y = conv(s, h)
+        assert np.max(np.abs(y - ref)) < 1e-12, z
+
+
+def pin_adjoint_dot(conv, adjoint, seed=16):
+    """The adjoint satisfies Re<g, y(s, h)> = Re<ds, s> = Re<dh, h> (a linear
+    map and its adjoint); convention grad = dL/dRe + i dL/dIm."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    for (Ns, M, F) in ((50, 7, 3), (300, 64, 2), (64, 64, 1), (33, 1, 2)):
+        s = _c64(g.normal(size=Ns) + 1j * g.normal(size=Ns))
+        h = _c64(g.normal(size=(F, M)) + 1j * g.normal(size=(F, M)))
+        gr = g.normal(size=(F, Ns - M + 1)) + 1j * g.normal(size=(F, Ns - M + 1))
+        y = conv(s, h)
+        ds, dh = adjoint(s, h, gr)
+        lhs = np.real(np.vdot(gr, y))
+        r1 = np.real(np.vdot(ds, s.astype(np.complex128)))
+        r2 = np.real(np.vdot(dh, h.astype(np.complex128)))
+        scale = np.linalg.norm(gr) * np.linalg.norm(y) + 1.0
+        assert abs(lhs - r1) < 1e-12 * scale, (Ns, M, F, lhs, r1)
+        assert abs(lhs - r2) < 1e-12 * scale, (Ns, M, F, lhs, r2)
+
+
+def weighted_power_loss(y, w):
+    """L = sum_f sum_j w[j] |y_f[j]|^2 in FP64."""
+    y = np.atleast_2d(y)
+    return float(np.sum(w[None, :] * (y.real ** 2 + y.imag ** 2)))
+
+
+def pin_adjoint_finite_difference(conv, adjoint, seed=17, Ns=4096, F=16, M=129,
+                                  h_filters=(0, 7, 15), n_s=512):
+    """FP64 central differences of L = sum w|y|^2 (quadratic, so the central
+    difference is exact up to rounding) against ds, dh with g = 2 w y.
+    Inputs lie on a 2^-10 grid and the step is 2^-6, so every perturbed input
+    is exact in FP32."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    s = quantized(g, Ns, 2.0 ** -10)
+    h = quantized(g, (F, M), 2.0 ** -10)
+    w = g.uniform(0, 1, Ns - M + 1)
+    y = conv(s, h)
+    grad_y = 2.0 * w[None, :] * y
+    ds, dh = adjoint(s, h, grad_y)
+    eps = 2.0 ** -6
+    worst = 0.0
+    # every real coordinate of the chosen filters
+    for f in h_filters:
+        for k in range(M):
+            for unit in (1.0, 1j):
+                hp = h[f].astype(np.complex128).copy()
+                hm = hp.copy()
+                hp[k] += eps * unit
+                hm[k] -= eps * unit
+                lp = weighted_power_loss(conv(s, _c64(hp)), w)
+                lm = weighted_power_loss(conv(s, _c64(hm)), w)
+                fd = (lp - lm) / (2 * eps)
+                an = dh[f, k].real if unit == 1.0 else dh[f, k].imag
+                worst = max(worst, abs(fd - an) / (abs(an) + 1e-3 * np.max(np.abs(dh))))
+    # seeded coordinates of s; only outputs j in [m-M+1, m] depend on s[m]
+    Nout = Ns - M + 1
+    ms = np.concatenate([[0, 1, M - 1, M, Ns // 2, Ns - M, Ns - 2, Ns - 1],
+                         g.integers(0, Ns, size=max(0, n_s - 8))])
+    sd = s.astype(np.complex128)
+    for m in ms:
+        j0, j1 = max(0, m - M + 1), min(Nout - 1, m)
+        for unit in (1.0, 1j):
+            sp = sd[j0:j1 + M].copy()
+            sm = sp.copy()
+            sp[m - j0] += eps * unit
+            sm[m - j0] -= eps * unit
+            lp = weighted_power_loss(conv(_c64(sp), h), w[j0:j1 + 1])
+            lm = weighted_power_loss(conv(_c64(sm), h), w[j0:j1 + 1])
+            fd = (lp - lm) / (2 * eps)
+            an = ds[m].real if unit == 1.0 else ds[m].imag
+            worst = max(worst, abs(fd - an) / (abs(an) + 1e-3 * np.max(np.abs(ds))))
+    assert worst < 1e-9, worst
+    return worst
+
+
+QUICK_PINS = (pin_golden_conv, pin_golden_adjoint, pin_bruteforce_dft, pin_delta_shift,
+              pin_linearity, pin_closed_forms, pin_adjoint_dot)

@@ -1,0 +1,141 @@
+"""The FP64 oracle pinned to the paper and to mathematics (CPU only)."""
+import ctypes
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import oracle_pins as P
+
+
+def _conv(s, h):
+    return oracle.conv(s, h)
+
+
+def _adj(s, h, g):
+    return oracle.adjoint(s, h, g)
+
+
+@pytest.mark.parametrize("pin", [P.pin_golden_conv, P.pin_golden_adjoint, P.pin_bruteforce_dft,
+                                 P.pin_fft_fullconv, P.pin_delta_shift, P.pin_linearity,
+                                 P.pin_closed_forms, P.pin_adjoint_dot])
+def test_oracle_pin(pin):
+    pin(_conv, _adj)
+
+
+def test_oracle_adjoint_finite_difference():
+    worst = P.pin_adjoint_finite_difference(_conv, _adj)
+    assert worst < 1e-9
+
+
+def test_oracle_conv_at_matches_conv():
+    g = np.random.Generator(np.random.PCG64(3))
+    s = (g.uniform(-1, 1, 1000) + 1j * g.uniform(-1, 1, 1000)).astype(np.complex64)
+    h = (g.normal(size=(4, 33)) + 1j * g.normal(size=(4, 33))).astype(np.complex64)
+    y = oracle.conv(s, h)
+    fi = g.integers(0, 4, 200)
+    ji = g.integers(0, y.shape[1], 200)
+    assert np.array_equal(oracle.conv_at(s, h, fi, ji), y[fi, ji])
+    with pytest.raises(ValueError):
+        oracle.conv_at(s, h, [4], [0])
+    with pytest.raises(ValueError):
+        oracle.conv_at(s, h, [0], [y.shape[1]])
+
+
+def test_oracle_rejects_bad_sizes():
+    s = np.zeros(4, np.complex64)
+    with pytest.raises(ValueError):
+        oracle.conv(s, np.zeros(5, np.complex64))
+    with pytest.raises(TypeError):
+        oracle.conv(s.astype(np.complex128), np.zeros(2, np.complex64))
+
+
+def test_oracle_thread_count_invariant():
+    """Each output is one sequential sum, so the thread count cannot change it."""
+    g = np.random.Generator(np.random.PCG64(4))
+    s = (g.uniform(-1, 1, 3000) + 1j * g.uniform(-1, 1, 3000)).astype(np.complex64)
+    h = (g.normal(size=(3, 65)) + 1j * g.normal(size=(3, 65))).astype(np.complex64)
+    n0 = oracle.threads()
+    try:
+        oracle.set_threads(1)
+        y1 = oracle.conv(s, h)
+        oracle.set_threads(max(2, n0))
+        y2 = oracle.conv(s, h)
+    finally:
+        oracle.set_threads(n0)
+    assert np.array_equal(y1, y2)
+
+
+# ------------------------------------------------------------ mutation test
+# Plausible mistakes planted in copies of the oracle source (never in the
+# oracle itself).  Each must be caught by at least one quick pin.
+MUTANTS = {
+    "drop_last_tap": ("for (int32_t k = 0; k < M; ++k) {\n        const int64_t n = j",
+                      "for (int32_t k = 0; k < M - 1; ++k) {\n        const int64_t n = j"),
+    "off_by_one_index": ("const int64_t n = j + (int64_t)M - 1 - k;",
+                         "const int64_t n = j + (int64_t)M - 1 - k + (k > 0);"),
+    "conjugated_tap": ("acc_im += sr * hi + si * hr;", "acc_im += si * hr - sr * hi;"),
+    "wrong_sign_re": ("acc_re += sr * hr - si * hi;", "acc_re += sr * hr + si * hi;"),
+    "adjoint_no_conj_h": ("acc_im += gi * hr - gr * hi;", "acc_im += gi * hr + gr * hi;"),
+    "adjoint_dh_index": ("const int64_t n = j + M - 1 - k;", "const int64_t n = j + k;"),
+    "adjoint_ds_edge": ("if (j < 0 || j >= Nout) continue;", "if (j < 0 || j >= Nout - 1) continue;"),
+}
+
+
+def _bind(path):
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.ols_oracle_conv.argtypes = [i64, vp, i32, i32, vp, vp]
+    lib.ols_oracle_adjoint.argtypes = [i64, vp, i32, i32, vp, vp, vp, vp]
+
+    def conv(s, h):
+        s = np.ascontiguousarray(s, np.complex64)
+        h = np.ascontiguousarray(h, np.complex64)
+        sq = h.ndim == 1
+        h2 = h[None] if sq else h
+        F, M = h2.shape
+        y = np.empty((F, len(s) - M + 1), np.complex128)
+        lib.ols_oracle_conv(len(s), s.ctypes.data, M, F, h2.ctypes.data, y.ctypes.data)
+        return y[0] if sq else y
+
+    def adjoint(s, h, g):
+        s = np.ascontiguousarray(s, np.complex64)
+        h = np.ascontiguousarray(h, np.complex64)
+        sq = h.ndim == 1
+        h2 = h[None] if sq else h
+        g2 = np.ascontiguousarray(np.atleast_2d(g), np.complex128)
+        F, M = h2.shape
+        ds = np.empty(len(s), np.complex128)
+        dh = np.empty((F, M), np.complex128)
+        lib.ols_oracle_adjoint(len(s), s.ctypes.data, M, F, h2.ctypes.data, g2.ctypes.data,
+                               ds.ctypes.data, dh.ctypes.data)
+        return ds, (dh[0] if sq else dh)
+
+    return conv, adjoint
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "ols_oracle.c")).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, "mutation anchor not unique: " + name
+    with tempfile.TemporaryDirectory() as d:
+        cpath = os.path.join(d, "mut.c")
+        with open(cpath, "w") as fh:
+            fh.write(src.replace(old, new))
+        so = os.path.join(d, "libmut.so")
+        subprocess.run(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                        "-std=c11", "-o", so, cpath], check=True)
+        conv, adjoint = _bind(so)
+        caught = []
+        for pin in P.QUICK_PINS:
+            try:
+                pin(conv, adjoint)
+            except AssertionError:
+                caught.append(pin.__name__)
+        assert caught, "no pin caught mutant " + name
