@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the fused overlap-and-save convolution on GB300.
+
+One step = one ``ols_convolve`` call over the whole workload: the filter bank
+(Ns = 2^23 complex64 samples, F = 32 filters of M = 257 taps, Hann-windowed,
+segment length N = 2048), inputs resident in HBM.  Metric: output samples per
+second, F * (Ns - M + 1) / time.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank convolves its own independent signal of the
+same size (weak scaling, no collective on the data path); timing is the max
+over ranks.  ``--impl reference`` times the FP64 CPU oracle instead (rank 0
+only), on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "output samples/s (F*(Ns-M+1))"
+UNIT = "samples/s"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1910_01972_gb300/csrc/ols_forward.cu", "paper_1910_01972_gb300/csrc/fft_regs.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_forward_bank_Ns8388608_F32_M257_N2048.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since that capture."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m_t or not m_h or m_h.group(1) != kernel_source_hash():
+        return None
+    return float(m_t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons."""
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.windows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "note": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and self.uuid not in parts[1]:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[4], parts[6:10]))
+            except (ValueError, IndexError):
+                continue
+        inwin = [r for r in rows if any(a - 0.05 <= r[0] <= b + 0.05 for a, b in self.windows)]
+        used = inwin if len(inwin) >= 3 else rows
+        if not used:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in used for i in range(4) if r[4][i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in used), "sm_max_mhz": max(r[2] for r in used),
+                "reasons": reasons, "samples": len(used),
+                "window": "timed region" if used is inwin else "whole run (timed region too short)"}
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_rate(s, h, seconds, max_outputs=None):
+    """Time the FP64 oracle on a prefix of the workload sized to ~seconds of
+    CPU work.  Returns (outputs/s, threads, sample description, prefix Ns, y_ref)."""
+    import oracle
+    F, M = h.shape
+    cal_ns = min(len(s), M - 1 + 2048)
+    t0 = time.perf_counter()
+    oracle.conv(s[:cal_ns], h)
+    t_cal = max(time.perf_counter() - t0, 1e-6)
+    per_out = t_cal / (F * (cal_ns - M + 1))
+    n_out = int(seconds / per_out / F)
+    if max_outputs:
+        n_out = min(n_out, max_outputs)
+    n_out = max(1, min(n_out, len(s) - M + 1))
+    ns = n_out + M - 1
+    t0 = time.perf_counter()
+    y_ref = oracle.conv(s[:ns], h)
+    dt = time.perf_counter() - t0
+    desc = "first %d samples of the signal (all %d filters, %d outputs per filter)" % (ns, F, n_out)
+    return F * n_out / dt, oracle.threads(), desc, ns, y_ref
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import synth
+    cfg = synth.PLAIN_BANK
+    s, h = synth.plain_inputs(cfg)
+    budget = 150.0
+    per_step = max(0.5, min(5.0, budget / max(1, args.steps + args.warmup)))
+    # size each step's sample once, then run W untimed + K timed steps
+    rate0, threads, desc, ns, _ = oracle_rate(s, h, per_step)
+    import oracle
+    for _ in range(args.warmup):
+        oracle.conv(s[:ns], h)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.conv(s[:ns], h)
+    dt = time.perf_counter() - t0
+    outputs = cfg.F * (ns - cfg.M + 1)
+    value = outputs * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg.name, "Ns": cfg.Ns, "F": cfg.F, "M": cfg.M, "N": cfg.N,
+                   "note": "FP64 direct convolution (Eq. 1) on host cores; each step is a bounded sample"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc + " per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our leg
+def run_ours(args):
+    import numpy as np
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import Plan, _native
+    from paper_1910_01972_gb300 import build as _build
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    _native.lib()
+
+    cfg = synth.PLAIN_BANK
+    s_np, h_np = synth.plain_inputs(cfg)
+    if rank:
+        # every rank convolves its own independent signal of the same size
+        s_np = synth.signal(synth.rng(cfg.index, salt=100 + rank), cfg.Ns)
+    plan = Plan(cfg.M, cfg.F, cfg.N)
+    q = plan.query(cfg.Ns)
+    Nout, L, nseg = q["Nout"], q["L"], q["nseg"]
+    s = torch.from_numpy(s_np).cuda()
+    h = torch.from_numpy(h_np).cuda()
+    plan.set_filters(h)
+    y = torch.empty((cfg.F, Nout), dtype=torch.complex64, device="cuda")
+    st = torch.cuda.current_stream()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+
+    for _ in range(max(3, args.warmup)):
+        plan.convolve(s, out=y)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.time()
+    e0.record(st)
+    for _ in range(args.steps):
+        plan.convolve(s, out=y)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    if dist is not None:
+        dist.barrier()
+    clocks.mark(t_host0, t_host1)
+    ms_total = e0.elapsed_time(e1)
+    launches = plan.last_launch_count() * args.steps
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    outputs = cfg.F * Nout
+    value = world * outputs / (ms_step * 1e-3)
+
+    # roofline of the (only) kernel: algorithmic bytes per launch / average launch time
+    alg_bytes = 8 * cfg.Ns + 8 * cfg.F * cfg.N + 8 * cfg.F * Nout
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    traffic = ncu_traffic()
+
+    # end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        s_host = torch.from_numpy(s_np).pin_memory()
+        y_host = torch.empty((cfg.F, Nout), dtype=torch.complex64, pin_memory=True)
+        plan.convolve_host(s_host, y_host)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.time()
+        e0.record(st)
+        for _ in range(args.e2e_steps):
+            plan.convolve_host(s_host, y_host)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        clocks.mark(t0, t1)
+        ms_e2e = (t1 - t0) * 1e3 / args.e2e_steps
+        if dist is not None:
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        cseg_chunks = plan.last_launch_count()
+        h2d = 8 * (cfg.Ns + (cseg_chunks - 1) * (cfg.M - 1))
+        e2e = {"value": world * outputs / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "steps": args.e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * cfg.F * Nout,
+               "path": "ols_convolve_host: pinned host buffers, chunked H2D / kernel / D2H on two streams"}
+        del y_host, s_host
+    clk = clocks.stop()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, threads, desc, ns, y_ref = oracle_rate(s_np, h_np, args.cpu_seconds)
+        got = y[:, : ns - cfg.M + 1].cpu().numpy()
+        err = max(float(np.linalg.norm(got[f] - y_ref[f]) / np.linalg.norm(y_ref[f])) for f in range(cfg.F))
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+               "gpu_rel_l2_on_sample": err}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "Ns": cfg.Ns, "F": cfg.F, "M": cfg.M, "N": cfg.N, "L": L, "nseg": nseg,
+                   "filters": "complex Gaussian x Hann, unit L2", "signal": "uniform[-1,1] re/im, seeded",
+                   "l2": "working set 2.2 GB > 129 MB L2: each step streams 2.15 GB of output through L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

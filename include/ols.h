@@ -1,0 +1,170 @@
+/*
+ * ols.h -- C ABI of the GB300 overlap-and-save (OLS) convolution library.
+ *
+ * The operation (paper: "GPU Fast Convolution via the Overlap-and-Save Method
+ * in Shared Memory", arXiv:1910.01972):
+ *
+ *   Eq. 1 (Sec. 1)  y[n] = sum_{k=0}^{M-1} s[n-k] h[k]
+ *
+ * evaluated for a bank of F filters by overlap-and-save (Sec. 3.2): the
+ * signal is cut into segments of N samples that overlap by M-1; each segment
+ * is Fourier transformed, multiplied point-wise by every filter's spectrum,
+ * inverse transformed, and its M-1 circularly aliased samples are dropped
+ * (Sec. 3.2, Fig. 1, Algorithm 2).  The result is the "valid" part of Eq. 1:
+ *
+ *   y_f[j] = sum_{k=0}^{M-1} s[j+M-1-k] h_f[k],   0 <= j < Nout = Ns-M+1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex values are interleaved FP32 pairs (re, im): a complex array of n
+ *   elements is 2n floats.  Every array is contiguous and row-major.
+ * - Pointers are DEVICE pointers owned by the caller unless a name ends in
+ *   _host; the library never frees caller memory.  Complex arrays must be
+ *   8-byte aligned.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Compute entry points only enqueue work: they do not
+ *   synchronise the host and do not allocate, so they can be captured in a
+ *   CUDA graph.  The plan must be used on the device that was current when
+ *   it was created.
+ * - Every entry point returns an ols_status and never aborts or prints.
+ *   Arguments are checked before any work is enqueued; on an error nothing is
+ *   enqueued.  Asynchronous kernel faults surface at the caller's next
+ *   synchronisation, as with any CUDA call.
+ * - Sizes: N (segment / FFT length) is a power of two in [256, 8192]; the
+ *   paper's kernels stop at 4096 (Sec. 2), the larger shared memory of the
+ *   target allows 8192.  1 <= M <= N, F >= 1, Ns >= M.
+ */
+#ifndef OLS_H
+#define OLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OLS_API __attribute__((visibility("default")))
+#else
+#define OLS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OLS_OK = 0,
+    OLS_ERR_INVALID = 1,      /* null / misaligned pointer, size out of range */
+    OLS_ERR_UNSUPPORTED = 2,  /* N not a power of two in [256, 8192], M > N, bad flag */
+    OLS_ERR_ALLOC = 3,        /* device or host allocation failed */
+    OLS_ERR_CUDA = 4,         /* a CUDA runtime call failed (including: no device) */
+    OLS_ERR_NOT_READY = 5,    /* filters were not set on the plan */
+    OLS_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+    OLS_ERR_WORKSPACE = 7     /* caller workspace missing or too small */
+} ols_status;
+
+typedef struct ols_plan_s *ols_plan_t;
+
+/* Plan flags (arithmetic of the plain convolution). */
+#define OLS_FLAG_FP32 0u
+
+/* Human-readable name of a status code (static storage; never NULL). */
+OLS_API const char *ols_status_string(int status);
+
+/* Library ABI version (major*100 + minor). */
+OLS_API int ols_version(void);
+
+/*
+ * Segment bookkeeping of Sec. 3.2 -- pure host arithmetic, needs no GPU.
+ * L = N - M + 1 valid samples per segment (M-1 aliased samples dropped);
+ * Nout = Ns - M + 1 outputs per filter; nseg = ceil(Nout / L) segments,
+ * segment i reading s[i*L, i*L + N) (zero past Ns) and writing
+ * y[f][i*L, min(i*L + L, Nout)).  Any output pointer may be NULL.
+ * Errors: OLS_ERR_INVALID if M < 1 or Ns < M; OLS_ERR_UNSUPPORTED if N is not
+ * a supported power of two or M > N.
+ */
+OLS_API int ols_geometry(int64_t N, int32_t M, int64_t Ns, int64_t *L, int64_t *nseg, int64_t *Nout);
+
+/*
+ * The library's internal spectral order -- pure host, needs no GPU.
+ * Sec. 3.3 notes that the point-wise product does not care about the order
+ * of the spectrum as long as signal and filter share it and the inverse
+ * transform consumes it, so the forward FFT skips the reordering step.  This
+ * returns, for each storage position q in [0, N), the frequency index
+ * nu[q] held there (a permutation of [0, N)).  nu: host array of N int32.
+ */
+OLS_API int ols_spectrum_order(int64_t N, int32_t *nu);
+
+/*
+ * Create a plan for segment length N, filter length M and F filters
+ * (Sec. 3.2; N = 0 lets the library pick N from M, F and the segment-length
+ * rule of Sec. 5: each N is best for a range of M).  Allocates the plan's
+ * device tables (filter spectra F*N complex, twiddles) on the current
+ * device.  flags: OLS_FLAG_FP32.
+ * Errors: INVALID (out == NULL, M < 1, F < 1), UNSUPPORTED (N, M > N, flags),
+ * CUDA / ALLOC from the device.  *out is NULL on error.
+ */
+OLS_API int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags);
+
+/* Release a plan and its device tables (synchronises the device first).
+ * NULL is accepted and ignored. */
+OLS_API int ols_plan_destroy(ols_plan_t plan);
+
+/* Plan parameters and the segment bookkeeping for a signal of Ns samples
+ * (Ns may be 0 to query only N, M, F).  Any output pointer may be NULL. */
+OLS_API int ols_plan_query(ols_plan_t plan, int64_t Ns, int64_t *N, int32_t *M, int32_t *F,
+                   int64_t *L, int64_t *nseg, int64_t *Nout);
+
+/*
+ * Filter-spectrum precompute (Algorithm 1 and 2: "forward FFT of the
+ * filters", done once before the convolution kernel runs; Fig. 1's first
+ * step).  h: device [F][M] complex.  Each filter is zero-padded to N and
+ * transformed in FP64 (exact index reduction of every twiddle exponent), the
+ * 1/N of the inverse transform is folded in, and the result is rounded to
+ * FP32 and stored in the plan in the kernel's internal spectral order and
+ * register layout.  Enqueued on `stream`; h may be freed once that work is
+ * done.  Errors: INVALID (plan or h NULL / misaligned), CUDA.
+ */
+OLS_API int ols_set_filters(ols_plan_t plan, const float *h, void *stream);
+
+/*
+ * Read back the plan's filter spectra in natural frequency order, FP32:
+ * H[f][nu] = (1/N) sum_k h_f[k] exp(-2 pi i nu k / N).  H: device [F][N]
+ * complex.  For tests and tooling.  Errors: INVALID, NOT_READY, CUDA.
+ */
+OLS_API int ols_get_spectra(ols_plan_t plan, float *H, void *stream);
+
+/*
+ * The fused OLS convolution (Algorithm 2, Sec. 3.3): one kernel; each
+ * segment of s is read from HBM once, forward-transformed in registers and
+ * shared memory, and for every filter multiplied by its spectrum, inverse
+ * transformed, stripped of its M-1 aliased samples and written once.
+ * s: device [Ns] complex.  y: device [F][Ns-M+1] complex (row f holds
+ * filter f's output).  s and y must not overlap.
+ * Errors: INVALID (NULL / misaligned pointer, Ns < M), NOT_READY (no
+ * filters), CUDA (launch failure).
+ */
+OLS_API int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream);
+
+/*
+ * The same convolution with HOST buffers (what a user outside the device
+ * calls, Sec. 4.4 discusses the PCI-e cost): s_host [Ns] complex, y_host
+ * [F][Ns-M+1] complex.  The signal is cut into chunks of whole segments;
+ * each chunk's input (with its M-1 halo) is copied host->device, convolved
+ * and copied device->host on a pipeline of streams so transfers overlap the
+ * kernels.  Pinned (page-locked) host memory is needed for the overlap;
+ * pageable memory works but serialises.  Allocates device staging buffers on
+ * first use and when a larger chunk is needed; returns after y_host is
+ * complete (synchronises `stream`'s work it enqueued).
+ * Errors: INVALID, NOT_READY, ALLOC, CUDA.
+ */
+OLS_API int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y_host,
+                      void *stream);
+
+/* Number of kernel launches the last ols_convolve on this plan enqueued
+ * (for launch accounting in benchmarks). */
+OLS_API int ols_last_launch_count(ols_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OLS_H */

@@ -1,0 +1,150 @@
+"""GB300-native overlap-and-save (OLS) convolution.
+
+Fused OLS convolution of a long complex signal with a bank of short filters
+(arXiv:1910.01972, Algorithm 2), as hand-written CUDA kernels for sm_103a
+behind a C ABI (``include/ols.h``).  This package is the thin Python side:
+``_native`` binds the C functions under their own names, and ``Plan`` passes
+torch tensors' device pointers and the current CUDA stream to them.  PyTorch
+supplies device memory and streams only; every step of the convolution runs
+in the library's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _native
+from ._native import OLSError, check
+
+__all__ = ["Plan", "OLSError", "geometry", "spectrum_order", "convolve"]
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _require(t: torch.Tensor, name: str, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.dtype != torch.complex64:
+        raise TypeError("%s must be complex64, got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
+
+
+def geometry(N: int, M: int, Ns: int):
+    """(L, nseg, Nout) of Sec. 3.2's segmentation; host arithmetic only."""
+    rc, L, nseg, Nout = _native.ols_geometry(N, M, Ns)
+    check(rc, "ols_geometry")
+    return L, nseg, Nout
+
+
+def spectrum_order(N: int):
+    """Frequency index held at each storage position of the internal spectrum."""
+    rc, nu = _native.ols_spectrum_order(N)
+    check(rc, "ols_spectrum_order")
+    return nu
+
+
+class Plan:
+    """A plan for F filters of M taps with segment length N (0 = automatic).
+
+    The plan lives on the CUDA device current at construction.
+    """
+
+    def __init__(self, M: int, F: int, N: int = 0, flags: int = _native.OLS_FLAG_FP32):
+        rc, handle = _native.ols_plan(int(N), int(M), int(F), int(flags))
+        check(rc, "ols_plan")
+        self._h = handle
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        rc, q = _native.ols_plan_query(self._h, 0)
+        check(rc, "ols_plan_query")
+        self.N, self.M, self.F, self.L = q["N"], q["M"], q["F"], q["L"]
+        self._filters = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.ols_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def query(self, Ns: int):
+        rc, q = _native.ols_plan_query(self._h, int(Ns))
+        check(rc, "ols_plan_query")
+        return q
+
+    def set_filters(self, h: torch.Tensor) -> None:
+        """h: [F][M] complex64 on the plan's device."""
+        _require(h, "h", self.device)
+        if tuple(h.shape) != (self.F, self.M):
+            raise ValueError("h must have shape [%d][%d]" % (self.F, self.M))
+        check(_native.ols_set_filters(self._h, h.data_ptr(), _stream_ptr(self.device)), "ols_set_filters")
+        self._filters = h
+
+    def spectra(self) -> torch.Tensor:
+        """The plan's filter spectra in natural order, [F][N] complex64 (1/N folded in)."""
+        H = torch.empty((self.F, self.N), dtype=torch.complex64, device=self.device)
+        check(_native.ols_get_spectra(self._h, H.data_ptr(), _stream_ptr(self.device)), "ols_get_spectra")
+        return H
+
+    def convolve(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Valid-mode convolution: s [Ns] -> y [F][Ns-M+1] (complex64, device)."""
+        _require(s, "s", self.device)
+        if s.dim() != 1:
+            raise ValueError("s must be 1-D")
+        Ns = s.shape[0]
+        if Ns < self.M:
+            raise ValueError("signal shorter than the filter (Ns < M)")
+        Nout = Ns - self.M + 1
+        if out is None:
+            out = torch.empty((self.F, Nout), dtype=torch.complex64, device=self.device)
+        else:
+            _require(out, "out", self.device)
+            if tuple(out.shape) != (self.F, Nout):
+                raise ValueError("out must have shape [F][Ns-M+1]")
+        check(_native.ols_convolve(self._h, s.data_ptr(), Ns, out.data_ptr(), _stream_ptr(self.device)),
+              "ols_convolve")
+        return out
+
+    def convolve_host(self, s_host: torch.Tensor, out_host: torch.Tensor | None = None) -> torch.Tensor:
+        """Host-buffer convolution (pinned CPU tensors give overlapped copies)."""
+        if s_host.device.type != "cpu":
+            raise ValueError("s_host must be a CPU tensor")
+        _require(s_host, "s_host")
+        Ns = s_host.shape[0]
+        if Ns < self.M:
+            raise ValueError("signal shorter than the filter (Ns < M)")
+        Nout = Ns - self.M + 1
+        if out_host is None:
+            out_host = torch.empty((self.F, Nout), dtype=torch.complex64, pin_memory=s_host.is_pinned())
+        _require(out_host, "out_host")
+        if tuple(out_host.shape) != (self.F, Nout) or out_host.device.type != "cpu":
+            raise ValueError("out_host must be a CPU tensor of shape [F][Ns-M+1]")
+        check(_native.ols_convolve_host(self._h, s_host.data_ptr(), Ns, out_host.data_ptr(),
+                                        _stream_ptr(self.device)), "ols_convolve_host")
+        return out_host
+
+    def last_launch_count(self) -> int:
+        return _native.ols_last_launch_count(self._h)
+
+
+def convolve(s: torch.Tensor, h: torch.Tensor, N: int = 0) -> torch.Tensor:
+    """One-shot convenience: plan, set filters, convolve (s [Ns], h [F][M])."""
+    if h.dim() == 1:
+        h = h.unsqueeze(0)
+    plan = Plan(h.shape[1], h.shape[0], N)
+    plan.set_filters(h.contiguous())
+    y = plan.convolve(s.contiguous())
+    torch.cuda.current_stream(plan.device).synchronize()
+    plan.close()
+    return y

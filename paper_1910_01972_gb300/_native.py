@@ -1,0 +1,135 @@
+"""ctypes binding of ``libols.so`` (C ABI declared in include/ols.h).
+
+Argument marshalling only: every function here has the name and argument
+order of its C counterpart and forwards plain integers and pointers.  The
+library must exist: there is no fallback of any kind, a missing or stale
+build raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libols.so")
+
+OLS_OK = 0
+OLS_ERR_INVALID = 1
+OLS_ERR_UNSUPPORTED = 2
+OLS_ERR_ALLOC = 3
+OLS_ERR_CUDA = 4
+OLS_ERR_NOT_READY = 5
+OLS_ERR_TIMEOUT = 6
+OLS_ERR_WORKSPACE = 7
+
+OLS_FLAG_FP32 = 0
+
+# (name, restype, argtypes) of every exported symbol declared in include/ols.h
+i32, i64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+vp, cint = ctypes.c_void_p, ctypes.c_int
+P_i64, P_i32 = ctypes.POINTER(i64), ctypes.POINTER(i32)
+SIGNATURES = [
+    ("ols_status_string", ctypes.c_char_p, [cint]),
+    ("ols_version", cint, []),
+    ("ols_geometry", cint, [i64, i32, i64, P_i64, P_i64, P_i64]),
+    ("ols_spectrum_order", cint, [i64, P_i32]),
+    ("ols_plan", cint, [ctypes.POINTER(vp), i64, i32, i32, u32]),
+    ("ols_plan_destroy", cint, [vp]),
+    ("ols_plan_query", cint, [vp, i64, P_i64, P_i32, P_i32, P_i64, P_i64, P_i64]),
+    ("ols_set_filters", cint, [vp, vp, vp]),
+    ("ols_get_spectra", cint, [vp, vp, vp]),
+    ("ols_convolve", cint, [vp, vp, i64, vp, vp]),
+    ("ols_convolve_host", cint, [vp, vp, i64, vp, vp]),
+    ("ols_last_launch_count", cint, [vp]),
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+class OLSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().ols_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__("%s: %s" % (where, msg))
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libols.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_1910_01972_gb300.build); there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def check(status: int, where: str) -> None:
+    if status != OLS_OK:
+        raise OLSError(status, where)
+
+
+def ols_status_string(status: int) -> str:
+    return lib().ols_status_string(status).decode()
+
+
+def ols_version() -> int:
+    return lib().ols_version()
+
+
+def ols_geometry(N: int, M: int, Ns: int):
+    L, nseg, Nout = i64(), i64(), i64()
+    rc = lib().ols_geometry(N, M, Ns, ctypes.byref(L), ctypes.byref(nseg), ctypes.byref(Nout))
+    return rc, L.value, nseg.value, Nout.value
+
+
+def ols_spectrum_order(N: int):
+    arr = (i32 * N)()
+    rc = lib().ols_spectrum_order(N, arr)
+    return rc, list(arr)
+
+
+def ols_plan(N: int, M: int, F: int, flags: int = OLS_FLAG_FP32):
+    h = vp()
+    rc = lib().ols_plan(ctypes.byref(h), N, M, F, flags)
+    return rc, h.value
+
+
+def ols_plan_destroy(plan) -> int:
+    return lib().ols_plan_destroy(plan)
+
+
+def ols_plan_query(plan, Ns: int = 0):
+    N, M, F, L, nseg, Nout = i64(), i32(), i32(), i64(), i64(), i64()
+    rc = lib().ols_plan_query(plan, Ns, ctypes.byref(N), ctypes.byref(M), ctypes.byref(F),
+                              ctypes.byref(L), ctypes.byref(nseg), ctypes.byref(Nout))
+    return rc, dict(N=N.value, M=M.value, F=F.value, L=L.value, nseg=nseg.value, Nout=Nout.value)
+
+
+def ols_set_filters(plan, h_ptr: int, stream: int) -> int:
+    return lib().ols_set_filters(plan, h_ptr, stream)
+
+
+def ols_get_spectra(plan, H_ptr: int, stream: int) -> int:
+    return lib().ols_get_spectra(plan, H_ptr, stream)
+
+
+def ols_convolve(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
+    return lib().ols_convolve(plan, s_ptr, Ns, y_ptr, stream)
+
+
+def ols_convolve_host(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
+    return lib().ols_convolve_host(plan, s_ptr, Ns, y_ptr, stream)
+
+
+def ols_last_launch_count(plan) -> int:
+    return lib().ols_last_launch_count(plan)

@@ -1,0 +1,321 @@
+// ols_api.cu -- the C ABI of include/ols.h: argument checks, plans, tables,
+// and the host-buffer pipeline.  All arithmetic of the convolution runs in
+// the kernels of ols_forward.cu and ols_precompute.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ols.h"
+#include "ols_internal.h"
+
+namespace ols {
+
+// Frequency index at each storage position of the forward FFT output.  The
+// forward passes are decimation in frequency: pass p splits the current
+// block of size B into r_p interleaved sub-blocks of stride s_p = B / r_p and
+// stores output k1 of its DFT in sub-block k1.  Position q therefore
+// decomposes into digits (k1 of pass 0 = q / s_0, ...), and the frequency is
+// those digits read in reverse significance: nu = k1_0 + r_0 (k1_1 + r_1 (...)).
+void spectral_order(int log2N, int32_t *nu) {
+    const PassPlan pp = make_pass_plan(log2N);
+    for (int q0 = 0; q0 < pp.N; ++q0) {
+        int q = q0, size = pp.N, mult = 1, v = 0;
+        for (int p = 0; p < pp.np; ++p) {
+            const int s = size / pp.radix[p];
+            v += (q / s) * mult;
+            q %= s;
+            mult *= pp.radix[p];
+            size = s;
+        }
+        nu[q0] = v;
+    }
+}
+
+static std::vector<float2> forward_twiddles(const PassPlan &pp) {
+    // pass p < np-1: entry (k-1) s + n' = W_{16 s}^{n' k}, k in [1, 16), n' in [0, s)
+    std::vector<float2> tw((size_t)pp.twn);
+    for (int p = 0; p + 1 < pp.np; ++p) {
+        const int s = pp.stride[p], B = 16 * s;
+        for (int k = 1; k < 16; ++k)
+            for (int n = 0; n < s; ++n) {
+                const long long e = ((long long)n * k) % B;
+                const double a = -2.0 * M_PI * (double)e / (double)B;
+                tw[(size_t)pp.tw_off[p] + (size_t)(k - 1) * s + n] =
+                    make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+    }
+    return tw;
+}
+
+static int log2_exact(int64_t N) {
+    if (N <= 0 || (N & (N - 1))) return -1;
+    int l = 0;
+    while ((int64_t(1) << l) < N) ++l;
+    return l;
+}
+
+static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
+
+static int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return OLS_OK;
+    if (e == cudaErrorMemoryAllocation) return OLS_ERR_ALLOC;
+    return OLS_ERR_CUDA;
+}
+
+// Segment-length rule (Sec. 3.2 and Sec. 5): a longer segment wastes a
+// smaller fraction M-1 of each FFT but costs log2(N) per point; pick the N
+// minimising the work per valid output, (N / L) (log2 N + c).
+static int64_t choose_N(int32_t M) {
+    double best = 1e300;
+    int64_t bestN = 0;
+    for (int l = kMinLog2N; l <= kMaxLog2N; ++l) {
+        const int64_t N = int64_t(1) << l;
+        if (M > N) continue;
+        const double L = (double)(N - M + 1);
+        const double cost = (double)N / L * ((double)l + 2.0);
+        if (cost < best) {
+            best = cost;
+            bestN = N;
+        }
+    }
+    return bestN;
+}
+
+static void free_staging(Staging &s) {
+    for (int i = 0; i < 2; ++i) {
+        if (s.in[i]) cudaFree(s.in[i]);
+        if (s.out[i]) cudaFree(s.out[i]);
+        if (s.st[i]) cudaStreamDestroy(s.st[i]);
+        if (s.ev_done[i]) cudaEventDestroy(s.ev_done[i]);
+        s.in[i] = s.out[i] = nullptr;
+        s.st[i] = nullptr;
+        s.ev_done[i] = nullptr;
+    }
+    if (s.ev_user) cudaEventDestroy(s.ev_user);
+    s.ev_user = nullptr;
+    s.in_cap = s.out_cap = 0;
+}
+
+static void free_plan(ols_plan_s *p) {
+    if (!p) return;
+    if (p->Hk) cudaFree(p->Hk);
+    if (p->tw) cudaFree(p->tw);
+    if (p->tw64) cudaFree(p->tw64);
+    if (p->nu) cudaFree(p->nu);
+    free_staging(p->stage);
+    delete p;
+}
+
+}  // namespace ols
+
+using namespace ols;
+
+extern "C" {
+
+const char *ols_status_string(int status) {
+    switch (status) {
+        case OLS_OK: return "OLS_OK";
+        case OLS_ERR_INVALID: return "OLS_ERR_INVALID: invalid argument";
+        case OLS_ERR_UNSUPPORTED: return "OLS_ERR_UNSUPPORTED: unsupported size or flag";
+        case OLS_ERR_ALLOC: return "OLS_ERR_ALLOC: allocation failed";
+        case OLS_ERR_CUDA: return "OLS_ERR_CUDA: CUDA runtime error";
+        case OLS_ERR_NOT_READY: return "OLS_ERR_NOT_READY: filters not set";
+        case OLS_ERR_TIMEOUT: return "OLS_ERR_TIMEOUT: bounded device wait gave up";
+        case OLS_ERR_WORKSPACE: return "OLS_ERR_WORKSPACE: workspace missing or too small";
+        default: return "OLS_ERR_UNKNOWN";
+    }
+}
+
+int ols_version(void) { return 100; }
+
+int ols_geometry(int64_t N, int32_t M, int64_t Ns, int64_t *L, int64_t *nseg, int64_t *Nout) {
+    if (M < 1 || Ns < M) return OLS_ERR_INVALID;
+    const int l = log2_exact(N);
+    if (l < kMinLog2N || l > kMaxLog2N || M > N) return OLS_ERR_UNSUPPORTED;
+    const int64_t Lv = N - M + 1;
+    const int64_t no = Ns - M + 1;
+    if (L) *L = Lv;
+    if (Nout) *Nout = no;
+    if (nseg) *nseg = (no + Lv - 1) / Lv;
+    return OLS_OK;
+}
+
+int ols_spectrum_order(int64_t N, int32_t *nu) {
+    if (!nu) return OLS_ERR_INVALID;
+    const int l = log2_exact(N);
+    if (l < kMinLog2N || l > kMaxLog2N) return OLS_ERR_UNSUPPORTED;
+    spectral_order(l, nu);
+    return OLS_OK;
+}
+
+int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
+    if (!out) return OLS_ERR_INVALID;
+    *out = nullptr;
+    if (M < 1 || F < 1) return OLS_ERR_INVALID;
+    if (flags != OLS_FLAG_FP32) return OLS_ERR_UNSUPPORTED;
+    if (N == 0) N = choose_N(M);
+    const int l = log2_exact(N);
+    if (l < kMinLog2N || l > kMaxLog2N || M > N) return OLS_ERR_UNSUPPORTED;
+
+    ols_plan_s *p = new (std::nothrow) ols_plan_s();
+    if (!p) return OLS_ERR_ALLOC;
+    p->N = N;
+    p->log2N = l;
+    p->M = M;
+    p->F = F;
+    p->flags = flags;
+    p->pp = make_pass_plan(l);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (e == cudaSuccess) e = cudaMalloc(&p->Hk, sizeof(float2) * (size_t)F * (size_t)N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tw, sizeof(float2) * (size_t)(p->pp.twn > 0 ? p->pp.twn : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->tw64, sizeof(double2) * (size_t)N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->nu, sizeof(int32_t) * (size_t)N);
+    if (e == cudaSuccess) {
+        std::vector<float2> tw = forward_twiddles(p->pp);
+        std::vector<int32_t> nu((size_t)N);
+        spectral_order(l, nu.data());
+        if (!tw.empty()) e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->nu, nu.data(), sizeof(int32_t) * nu.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = launch_tw64(p->tw64, (int)N, 0);
+    if (e == cudaSuccess) e = prepare_forward(*p);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return status_of(e);
+    }
+    *out = p;
+    return OLS_OK;
+}
+
+int ols_plan_destroy(ols_plan_t plan) {
+    if (!plan) return OLS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(plan);
+    return status_of(e);
+}
+
+int ols_plan_query(ols_plan_t plan, int64_t Ns, int64_t *N, int32_t *M, int32_t *F, int64_t *L,
+                   int64_t *nseg, int64_t *Nout) {
+    if (!plan) return OLS_ERR_INVALID;
+    if (N) *N = plan->N;
+    if (M) *M = plan->M;
+    if (F) *F = plan->F;
+    if (Ns == 0) {
+        if (L) *L = plan->N - plan->M + 1;
+        if (nseg) *nseg = 0;
+        if (Nout) *Nout = 0;
+        return OLS_OK;
+    }
+    return ols_geometry(plan->N, plan->M, Ns, L, nseg, Nout);
+}
+
+int ols_set_filters(ols_plan_t plan, const float *h, void *stream) {
+    if (!plan || !h || !aligned8(h)) return OLS_ERR_INVALID;
+    cudaError_t e = launch_spectra(reinterpret_cast<const float2 *>(h), plan->M, plan->F, plan->log2N,
+                                   plan->nu, plan->tw64, plan->Hk, (cudaStream_t)stream);
+    if (e != cudaSuccess) return status_of(e);
+    plan->filters_ready = true;
+    return OLS_OK;
+}
+
+int ols_get_spectra(ols_plan_t plan, float *H, void *stream) {
+    if (!plan || !H || !aligned8(H)) return OLS_ERR_INVALID;
+    if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    return status_of(launch_spectra_natural(plan->Hk, plan->F, plan->log2N, plan->nu,
+                                            reinterpret_cast<float2 *>(H), (cudaStream_t)stream));
+}
+
+int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream) {
+    if (!plan || !s || !y || !aligned8(s) || !aligned8(y)) return OLS_ERR_INVALID;
+    if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    int64_t L, nseg, Nout;
+    int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
+    if (rc != OLS_OK) return rc;
+    int launches = 0;
+    cudaError_t e = launch_forward(*plan, reinterpret_cast<const float2 *>(s), Ns, reinterpret_cast<float2 *>(y),
+                                   L, nseg, Nout, (cudaStream_t)stream, &launches);
+    plan->last_launches = launches;
+    return status_of(e);
+}
+
+int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y_host, void *stream) {
+    if (!plan || !s_host || !y_host || !aligned8(s_host) || !aligned8(y_host)) return OLS_ERR_INVALID;
+    if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    int64_t L, nseg, Nout;
+    int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
+    if (rc != OLS_OK) return rc;
+    const int64_t M = plan->M, F = plan->F;
+    // Whole segments per chunk: aim at ~64 MB of output per chunk.
+    const int64_t target = (int64_t)64 << 20;
+    int64_t cseg = target / (int64_t)(sizeof(float2) * F * L);
+    if (cseg < 1) cseg = 1;
+    if (cseg > nseg) cseg = nseg;
+    const int64_t cout = cseg * L;           // outputs per full chunk
+    const int64_t cin = cout + M - 1;        // inputs per full chunk
+    Staging &st = plan->stage;
+    cudaError_t e = cudaSuccess;
+    if (!st.st[0]) {
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&st.st[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev_done[i], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev_user, cudaEventDisableTiming);
+        if (e != cudaSuccess) return status_of(e);
+    }
+    if (st.in_cap < cin || st.out_cap < F * cout) {
+        for (int i = 0; i < 2; ++i) {
+            if (st.in[i]) cudaFree(st.in[i]);
+            if (st.out[i]) cudaFree(st.out[i]);
+            st.in[i] = st.out[i] = nullptr;
+        }
+        st.in_cap = st.out_cap = 0;
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaMalloc(&st.in[i], sizeof(float2) * (size_t)cin);
+            if (e == cudaSuccess) e = cudaMalloc(&st.out[i], sizeof(float2) * (size_t)(F * cout));
+        }
+        if (e != cudaSuccess) return status_of(e);
+        st.in_cap = cin;
+        st.out_cap = F * cout;
+    }
+    // Order after the caller's prior work on `stream` (e.g. ols_set_filters).
+    e = cudaEventRecord(st.ev_user, (cudaStream_t)stream);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st.st[i], st.ev_user, 0);
+    const float2 *sh = reinterpret_cast<const float2 *>(s_host);
+    float2 *yh = reinterpret_cast<float2 *>(y_host);
+    int launches = 0;
+    const int64_t nchunk = (nseg + cseg - 1) / cseg;
+    for (int64_t c = 0; c < nchunk && e == cudaSuccess; ++c) {
+        const int b = (int)(c & 1);
+        cudaStream_t cs = st.st[b];
+        const int64_t o0 = c * cout;                                   // first output of the chunk
+        const int64_t nout_c = (Nout - o0) < cout ? (Nout - o0) : cout;
+        const int64_t nin_c = nout_c + M - 1;                          // s[o0, o0 + nin_c)
+        e = cudaMemcpyAsync(st.in[b], sh + o0, sizeof(float2) * (size_t)nin_c, cudaMemcpyHostToDevice, cs);
+        int64_t Lc, nsegc, Noutc;
+        if (e == cudaSuccess) {
+            ols_geometry(plan->N, plan->M, nin_c, &Lc, &nsegc, &Noutc);
+            int l = 0;
+            e = launch_forward(*plan, st.in[b], nin_c, st.out[b], Lc, nsegc, Noutc, cs, &l);
+            launches += l;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(yh + o0, sizeof(float2) * (size_t)Nout, st.out[b], sizeof(float2) * (size_t)nout_c,
+                                  sizeof(float2) * (size_t)nout_c, (size_t)F, cudaMemcpyDeviceToHost, cs);
+    }
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e2 = cudaStreamSynchronize(st.st[i]);
+        if (e == cudaSuccess) e = e2;
+    }
+    plan->last_launches = launches;
+    return status_of(e);
+}
+
+int ols_last_launch_count(ols_plan_t plan) { return plan ? plan->last_launches : -1; }
+
+}  // extern "C"

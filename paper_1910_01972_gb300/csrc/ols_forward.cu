@@ -1,0 +1,255 @@
+// ols_forward.cu -- the fused overlap-and-save convolution kernel (FP32).
+//
+// Algorithm 2 / Sec. 3.3 of the paper: one kernel; a thread-block owns a
+// segment; the segment's forward FFT is done on chip and its spectrum kept
+// in registers (Sec. 3.3: "stores segment samples, which are now in the
+// frequency domain, into registers"), then for every filter: point-wise
+// product with the filter's precomputed spectrum, inverse FFT, removal of
+// the M-1 aliased samples, store (Sec. 3.2).
+//
+// GB300 design:
+// * Each thread holds 16 complex points; a segment of N points uses N/16
+//   threads.  The FFT is a sequence of radix-16 passes (one 16-point DFT per
+//   thread, all rotations compile-time constants) plus one pass of radix
+//   2/4/8/16 at stride 1; passes exchange data through shared memory.
+// * Forward: decimation in frequency, natural-order input, digit-reversed
+//   spectrum.  Inverse: the exact reverse of the passes (decimation in time),
+//   digit-reversed input, natural-order output.  No reordering step (Sec. 3.3
+//   notes the order is irrelevant to the point-wise product).
+// * The spectrum after the last forward pass sits in the registers the first
+//   inverse pass needs, so the per-filter loop starts from registers; the
+//   filter spectra are pre-laid-out so each thread's 16 values arrive in
+//   eight coalesced 16-byte loads.
+// * Shared-memory positions are padded by one slot per 16 (q -> q + q/16):
+//   every pass's accesses are then bank-conflict free for 64-bit loads and
+//   stores, and every address is a per-thread base plus a compile-time
+//   offset.  Two exchange buffers alternate, so one barrier per exchange.
+// * Global loads and stores: for each register k, consecutive threads touch
+//   consecutive samples (fully coalesced); the valid-output test is one
+//   unsigned compare per sample.
+// * Persistent grid: resident blocks loop over segments, loading the
+//   twiddle tables into shared memory once.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "fft_regs.cuh"
+#include "ols_internal.h"
+
+namespace ols {
+
+template <int LOG2N>
+struct Geo {
+    static constexpr int N = 1 << LOG2N;
+    static constexpr int T = N / 16;
+    static constexpr int NP = (LOG2N + 3) / 4;
+    static constexpr int RL = (LOG2N % 4) ? (1 << (LOG2N % 4)) : 16;
+    static constexpr int SEGS = T >= 128 ? 1 : 128 / T;
+    static constexpr int BLOCK = T * SEGS;
+    static constexpr int PADN = N + N / 16;
+    __host__ __device__ static constexpr int stride(int p) { return p == NP - 1 ? 1 : (N >> (4 * (p + 1))); }
+    __host__ __device__ static constexpr int radix(int p) { return p == NP - 1 ? RL : 16; }
+    __host__ __device__ static constexpr int tw_off(int p) {
+        int o = 0;
+        for (int i = 0; i < p; ++i) o += 15 * stride(i);
+        return o;
+    }
+    static constexpr int TWN = tw_off(NP - 1);
+    static constexpr int TWN_PAD = (TWN + 1) & ~1;   // keep the buffers 16-byte aligned
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * 2 * PADN);
+};
+
+// Padded shared-memory base of thread t in the layout of pass P:
+// positions (t / s) * 16 s + (t % s) + k s, padded q -> q + q / 16.
+template <int LOG2N, int P>
+__device__ __forceinline__ int pad_base(int t) {
+    constexpr int s = Geo<LOG2N>::stride(P);
+    const int q = (t / s) * 16 * s + (t % s);
+    return q + (q >> 4);
+}
+template <int LOG2N, int P>
+__device__ __forceinline__ constexpr int pad_off(int k) {
+    constexpr int s = Geo<LOG2N>::stride(P);
+    return k * s + ((k * s) >> 4);
+}
+
+// Write x in the layout of pass PW, barrier, read it back in the layout of PR.
+template <int LOG2N, int PW, int PR>
+__device__ __forceinline__ void exchange(float2 *x, float2 *buf, int t) {
+    const int bw = pad_base<LOG2N, PW>(t);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) buf[bw + pad_off<LOG2N, PW>(k)] = x[k];
+    __syncthreads();
+    const int br = pad_base<LOG2N, PR>(t);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = buf[br + pad_off<LOG2N, PR>(k)];
+}
+
+// Multiply element k of pass P's 16-point group by W_{16 s}^{(t mod s) k}
+// (conjugated for the inverse).
+template <int LOG2N, int P, bool INV>
+__device__ __forceinline__ void twiddle(float2 *x, const float2 *tw, int t) {
+    using G = Geo<LOG2N>;
+    constexpr int s = G::stride(P);
+    const float2 *w = tw + G::tw_off(P) + (t % s);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) x[k] = ctw<INV>(x[k], w[(k - 1) * s]);
+}
+
+template <int LOG2N, int P>
+__device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {
+    using G = Geo<LOG2N>;
+    dft_groups<G::radix(P), false>(x);
+    if constexpr (P < G::NP - 1) {
+        twiddle<LOG2N, P, false>(x, tw, t);
+        exchange<LOG2N, P, P + 1>(x, bufs + (xc & 1) * G::PADN, t);
+        ++xc;
+        forward_passes<LOG2N, P + 1>(x, bufs, tw, t, xc);
+    }
+}
+
+// x holds pass P+1's layout (or pass NP-1's when P == NP-1); runs the
+// inverse of passes P, P-1, ..., 0.
+template <int LOG2N, int P>
+__device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {
+    using G = Geo<LOG2N>;
+    if constexpr (P < G::NP - 1) {
+        exchange<LOG2N, P + 1, P>(x, bufs + (xc & 1) * G::PADN, t);
+        ++xc;
+        twiddle<LOG2N, P, true>(x, tw, t);
+    }
+    dft_groups<G::radix(P), true>(x);
+    if constexpr (P > 0) inverse_passes<LOG2N, P - 1>(x, bufs, tw, t, xc);
+}
+
+template <int LOG2N>
+__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK)
+ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
+                   const float2 *__restrict__ twg, float2 *__restrict__ y, int M, int F,
+                   long long L, long long nseg, long long Nout) {
+    using G = Geo<LOG2N>;
+    extern __shared__ float4 smem_raw[];
+    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+    float2 *tw = smem;
+    const int slot = threadIdx.x / G::T;
+    const int t = threadIdx.x % G::T;
+    float2 *bufs = smem + G::TWN_PAD + slot * 2 * G::PADN;
+
+    for (int i = threadIdx.x; i < G::TWN; i += G::BLOCK) tw[i] = twg[i];
+    __syncthreads();
+
+    const int lo = M - 1;                      // aliased samples per segment
+    int xc = 0;
+    const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
+    for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const long long seg = blk * G::SEGS + slot;
+        const bool active = seg < nseg;
+        const long long start = seg * L;
+
+        // Segment load: samples start + k T + t, zero past Ns.
+        float2 X[16];
+        {
+            const long long avail = active ? (Ns - start) : 0;
+            const int lim = (int)(avail < G::N ? avail : G::N);
+            const float2 *src = sig + (active ? start : 0) + t;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+        }
+        forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
+
+        // Valid outputs of this segment: n in [lo, lo + span), n = k T + t.
+        long long rem = active ? (Nout - start) : 0;
+        const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
+        const long long obase = start - lo;
+
+        for (int f = 0; f < F; ++f) {
+            float2 x[16];
+            const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) {
+                const float4 h = __ldg(hp + j2 * G::T);
+                x[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
+                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
+            }
+            inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
+            float2 *dst = y + (size_t)f * (size_t)Nout;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int n = k * G::T + t;
+                if ((unsigned)(n - lo) < (unsigned)span) dst[obase + n] = x[k];
+            }
+        }
+    }
+}
+
+template <int LOG2N>
+static cudaError_t prepare_one(ols_plan_s &p) {
+    using G = Geo<LOG2N>;
+    cudaError_t e = cudaFuncSetAttribute(ols_forward_kernel<LOG2N>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_forward_kernel<LOG2N>, G::BLOCK, G::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    p.fwd_grid_cap = per_sm * p.sm_count;
+    return cudaSuccess;
+}
+
+template <int LOG2N>
+static cudaError_t launch_one(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L,
+                              int64_t nseg, int64_t Nout, cudaStream_t st) {
+    using G = Geo<LOG2N>;
+    const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
+    const int grid = (int)(nblk < p.fwd_grid_cap ? nblk : p.fwd_grid_cap);
+    ols_forward_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM, st>>>(
+        s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y, p.M, p.F, L, nseg, Nout);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_forward(ols_plan_s &p) {
+    switch (p.log2N) {
+        case 8: return prepare_one<8>(p);
+        case 9: return prepare_one<9>(p);
+        case 10: return prepare_one<10>(p);
+        case 11: return prepare_one<11>(p);
+        case 12: return prepare_one<12>(p);
+        case 13: return prepare_one<13>(p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_forward(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L,
+                           int64_t nseg, int64_t Nout, cudaStream_t st, int *launches) {
+    *launches = 1;
+    switch (p.log2N) {
+        case 8: return launch_one<8>(p, s, Ns, y, L, nseg, Nout, st);
+        case 9: return launch_one<9>(p, s, Ns, y, L, nseg, Nout, st);
+        case 10: return launch_one<10>(p, s, Ns, y, L, nseg, Nout, st);
+        case 11: return launch_one<11>(p, s, Ns, y, L, nseg, Nout, st);
+        case 12: return launch_one<12>(p, s, Ns, y, L, nseg, Nout, st);
+        case 13: return launch_one<13>(p, s, Ns, y, L, nseg, Nout, st);
+        default: *launches = 0; return cudaErrorInvalidValue;
+    }
+}
+
+// Host mirror of Geo<>: the twiddle tables and spectral order are built from it.
+PassPlan make_pass_plan(int log2N) {
+    PassPlan pp{};
+    pp.log2N = log2N;
+    pp.N = 1 << log2N;
+    pp.T = pp.N / 16;
+    pp.np = (log2N + 3) / 4;
+    const int rl = (log2N % 4) ? (1 << (log2N % 4)) : 16;
+    int off = 0;
+    for (int p = 0; p < pp.np; ++p) {
+        pp.radix[p] = (p == pp.np - 1) ? rl : 16;
+        pp.stride[p] = (p == pp.np - 1) ? 1 : (pp.N >> (4 * (p + 1)));
+        pp.tw_off[p] = off;
+        if (p < pp.np - 1) off += 15 * pp.stride[p];
+    }
+    pp.twn = off;
+    return pp;
+}
+
+}  // namespace ols

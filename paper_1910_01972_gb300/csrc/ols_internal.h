@@ -1,0 +1,76 @@
+// ols_internal.h -- plan object and kernel launchers shared by the library's
+// translation units (not part of the public ABI, see include/ols.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ols.h"
+
+namespace ols {
+
+constexpr int kMinLog2N = 8;   // N = 256
+constexpr int kMaxLog2N = 13;  // N = 8192
+
+// Forward passes of the in-register/shared-memory FFT for N = 2^log2N:
+// radix-16 passes first (strides N/16, N/256, ...), then one pass of the
+// remaining radix (2, 4, 8 or 16) at stride 1.  Kept in one place so host
+// tables and device index math agree.
+struct PassPlan {
+    int log2N;
+    int N;
+    int T;       // threads per segment (N / 16): each thread holds 16 points
+    int np;      // number of passes
+    int radix[4];
+    int stride[4];
+    int tw_off[4];
+    int twn;     // twiddle entries of passes 0 .. np-2
+};
+PassPlan make_pass_plan(int log2N);
+
+// Frequency index held at each storage position of the forward FFT output.
+void spectral_order(int log2N, int32_t *nu);
+
+struct Staging {            // device buffers of ols_convolve_host
+    float2 *in[2] = {nullptr, nullptr};
+    float2 *out[2] = {nullptr, nullptr};
+    int64_t in_cap = 0, out_cap = 0;   // elements per buffer
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t ev_user = nullptr, ev_done[2] = {nullptr, nullptr};
+};
+
+}  // namespace ols
+
+struct ols_plan_s {
+    int device = 0;
+    int sm_count = 0;
+    int64_t N = 0;
+    int log2N = 0;
+    int32_t M = 0, F = 0;
+    uint32_t flags = 0;
+    bool filters_ready = false;
+    ols::PassPlan pp{};
+    float2 *Hk = nullptr;        // [F][N] spectra in kernel layout (FP32)
+    float2 *tw = nullptr;        // forward twiddles (FP32), pp.twn entries
+    double2 *tw64 = nullptr;     // W_N^m, m in [0, N) (FP64)
+    int32_t *nu = nullptr;       // spectral order (device copy)
+    int fwd_grid_cap = 0;        // resident blocks of the forward kernel
+    int last_launches = 0;
+    ols::Staging stage;
+};
+
+namespace ols {
+
+// Forward fused OLS (Algorithm 2).  Returns a cudaError_t.
+cudaError_t launch_forward(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y,
+                           int64_t L, int64_t nseg, int64_t Nout, cudaStream_t st, int *launches);
+// Occupancy / attribute set-up of the forward kernel for p.log2N.
+cudaError_t prepare_forward(ols_plan_s &p);
+// FP64 precompute kernels.
+cudaError_t launch_tw64(double2 *tw64, int N, cudaStream_t st);
+cudaError_t launch_spectra(const float2 *h, int M, int F, int log2N, const int32_t *nu,
+                           const double2 *tw64, float2 *Hk, cudaStream_t st);
+cudaError_t launch_spectra_natural(const float2 *Hk, int F, int log2N, const int32_t *nu,
+                                   float2 *H, cudaStream_t st);
+
+}  // namespace ols
