@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--ns", type=int, default=0, help="override the signal length (profiling a smaller case)")
     return ap.parse_args()
 
 
@@ -220,6 +221,9 @@ def run_ours(args):
     _native.lib()
 
     cfg = synth.PLAIN_BANK
+    if args.ns:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, Ns=args.ns, name=cfg.name.replace("Ns8388608", "Ns%d" % args.ns))
     s_np, h_np = synth.plain_inputs(cfg)
     if rank:
         # every rank convolves its own independent signal of the same size
@@ -318,7 +322,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg.name, "Ns": cfg.Ns, "F": cfg.F, "M": cfg.M, "N": cfg.N, "L": L, "nseg": nseg,
                    "filters": "complex Gaussian x Hann, unit L2", "signal": "uniform[-1,1] re/im, seeded",
-                   "l2": "working set 2.2 GB > 129 MB L2: each step streams 2.15 GB of output through L2",
+                   "l2": "working set %.2f GB > 129 MB L2: each step streams %.2f GB of output through L2, "
+                         "evicting the previous step's data (no separate flush)" % (
+                             (8 * cfg.Ns + 8 * cfg.F * Nout) / 1e9, 8 * cfg.F * Nout / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes},

@@ -7,14 +7,39 @@
 // compile-time constant.  INV selects the sign of the exponent:
 //   forward  X[k] = sum_n x[n] exp(-2 pi i n k / r)
 //   inverse  x[n] = sum_k X[k] exp(+2 pi i n k / r)   (unnormalised)
+//
+// The kernels are issue-bound: every FP32, load/store and integer
+// instruction competes for one issue slot per scheduler and cycle.  Complex
+// additions therefore use the packed two-lane FP32 add of sm_100+
+// (__fadd2_rn: one instruction for re and im, each lane rounded exactly like
+// a scalar add, so results are bitwise those of scalar code).  Where one
+// operand is multiplied by +-i the lanes cross, and two scalar adds are used.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace ols {
 
+#ifndef OLS_PACKED_ADD
+#define OLS_PACKED_ADD 1
+#endif
+#if OLS_PACKED_ADD
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+#else
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
+
+// a + r b and a - r b with r = -i (forward) or +i (inverse): lanes cross, scalar adds.
+template <bool INV>
+__device__ __forceinline__ float2 add_rot(float2 a, float2 b) {
+    return INV ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 sub_rot(float2 a, float2 b) {
+    return INV ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
+}
 
 // a * b
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -74,11 +99,23 @@ __device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
 template <bool INV>
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
     const float2 u0 = cadd(a0, a2), u1 = csub(a0, a2);
-    const float2 v0 = cadd(a1, a3), v1 = rot_quarter<INV>(csub(a1, a3));
+    const float2 v0 = cadd(a1, a3), d = csub(a1, a3);
     a0 = cadd(u0, v0);
     a2 = csub(u0, v0);
-    a1 = cadd(u1, v1);
-    a3 = csub(u1, v1);
+    a1 = add_rot<INV>(u1, d);     // u1 + r (a1 - a3)
+    a3 = sub_rot<INV>(u1, d);
+}
+
+// dft4 of (a0, a1, r a2, a3), r = -i (forward) / +i (inverse): the rotation of
+// a2 is folded into the first adds.
+template <bool INV>
+__device__ __forceinline__ void dft4_r2(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+    const float2 u0 = add_rot<INV>(a0, a2), u1 = sub_rot<INV>(a0, a2);
+    const float2 v0 = cadd(a1, a3), d = csub(a1, a3);
+    a0 = cadd(u0, v0);
+    a2 = csub(u0, v0);
+    a1 = add_rot<INV>(u1, d);
+    a3 = sub_rot<INV>(u1, d);
 }
 
 // 8-point DFT in place on x[0..7] (natural order in and out): 8 = 4 x 2.
@@ -88,13 +125,17 @@ __device__ __forceinline__ void dft8(float2 *x) {
     dft4<INV>(x[0], x[2], x[4], x[6]);   // n2 = 0 -> A[k1][0] at x[2 k1]
     dft4<INV>(x[1], x[3], x[5], x[7]);   // n2 = 1 -> A[k1][1] at x[2 k1 + 1]
     x[3] = rot16<2, INV>(x[3]);          // W8^1
-    x[5] = rot16<4, INV>(x[5]);          // W8^2
-    x[7] = rot16<6, INV>(x[7]);          // W8^3
+    x[7] = rot16<6, INV>(x[7]);          // W8^3  (W8^2 = r on x[5] is folded below)
     float2 y[8];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
-        y[k1] = cadd(x[2 * k1], x[2 * k1 + 1]);
-        y[k1 + 4] = csub(x[2 * k1], x[2 * k1 + 1]);
+        if (k1 == 2) {
+            y[k1] = add_rot<INV>(x[4], x[5]);
+            y[k1 + 4] = sub_rot<INV>(x[4], x[5]);
+        } else {
+            y[k1] = cadd(x[2 * k1], x[2 * k1 + 1]);
+            y[k1 + 4] = csub(x[2 * k1], x[2 * k1 + 1]);
+        }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[k] = y[k];
@@ -111,13 +152,14 @@ __device__ __forceinline__ void dft16(float2 *x) {
     x[6] = rot16<2, INV>(x[6]);
     x[7] = rot16<3, INV>(x[7]);
     x[9] = rot16<2, INV>(x[9]);
-    x[10] = rot16<4, INV>(x[10]);
     x[11] = rot16<6, INV>(x[11]);
     x[13] = rot16<3, INV>(x[13]);
     x[14] = rot16<6, INV>(x[14]);
     x[15] = rot16<9, INV>(x[15]);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+    dft4<INV>(x[0], x[1], x[2], x[3]);
+    dft4<INV>(x[4], x[5], x[6], x[7]);
+    dft4_r2<INV>(x[8], x[9], x[10], x[11]);    // x[10] carries W16^4 = r
+    dft4<INV>(x[12], x[13], x[14], x[15]);
     // x[4 k1 + k2] = X[k1 + 4 k2]; return natural order
     float2 y[16];
 #pragma unroll

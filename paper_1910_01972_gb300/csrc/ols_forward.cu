@@ -35,6 +35,23 @@
 #include "fft_regs.cuh"
 #include "ols_internal.h"
 
+// Tuning knobs (compile-time; defaults are the measured best on GB300).
+#ifndef OLS_PREFETCH_H
+#define OLS_PREFETCH_H 1     // load filter f+1's spectrum while filter f is transformed
+#endif
+#ifndef OLS_H_L2ONLY
+#define OLS_H_L2ONLY 0       // 1: spectra bypass L1 (__ldcg) instead of __ldg
+#endif
+#ifndef OLS_XBUFS
+#define OLS_XBUFS 2          // exchange buffers per segment (2: one barrier per exchange)
+#endif
+#ifndef OLS_TW_GLOBAL
+#define OLS_TW_GLOBAL 1      // twiddles read through L1 (1) or staged in shared memory (0)
+#endif
+#ifndef OLS_WARPS_PER_SM
+#define OLS_WARPS_PER_SM 16  // resident warps per SM the register budget must allow
+#endif
+
 namespace ols {
 
 template <int LOG2N>
@@ -45,6 +62,7 @@ struct Geo {
     static constexpr int RL = (LOG2N % 4) ? (1 << (LOG2N % 4)) : 16;
     static constexpr int SEGS = T >= 128 ? 1 : 128 / T;
     static constexpr int BLOCK = T * SEGS;
+    static constexpr int MINB = (OLS_WARPS_PER_SM * 32 + BLOCK - 1) / BLOCK;
     static constexpr int PADN = N + N / 16;
     __host__ __device__ static constexpr int stride(int p) { return p == NP - 1 ? 1 : (N >> (4 * (p + 1))); }
     __host__ __device__ static constexpr int radix(int p) { return p == NP - 1 ? RL : 16; }
@@ -54,8 +72,9 @@ struct Geo {
         return o;
     }
     static constexpr int TWN = tw_off(NP - 1);
-    static constexpr int TWN_PAD = (TWN + 1) & ~1;   // keep the buffers 16-byte aligned
-    static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * 2 * PADN);
+    static constexpr int TWN_PAD = OLS_TW_GLOBAL ? 0 : ((TWN + 1) & ~1);   // keep buffers 16-byte aligned
+    static constexpr int XBUFS = OLS_XBUFS;
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * XBUFS * PADN);
 };
 
 // Padded shared-memory base of thread t in the layout of pass P:
@@ -75,6 +94,7 @@ __device__ __forceinline__ constexpr int pad_off(int k) {
 // Write x in the layout of pass PW, barrier, read it back in the layout of PR.
 template <int LOG2N, int PW, int PR>
 __device__ __forceinline__ void exchange(float2 *x, float2 *buf, int t) {
+    if constexpr (Geo<LOG2N>::XBUFS == 1) __syncthreads();   // previous readers of buf are done
     const int bw = pad_base<LOG2N, PW>(t);
 #pragma unroll
     for (int k = 0; k < 16; ++k) buf[bw + pad_off<LOG2N, PW>(k)] = x[k];
@@ -92,7 +112,14 @@ __device__ __forceinline__ void twiddle(float2 *x, const float2 *tw, int t) {
     constexpr int s = G::stride(P);
     const float2 *w = tw + G::tw_off(P) + (t % s);
 #pragma unroll
-    for (int k = 1; k < 16; ++k) x[k] = ctw<INV>(x[k], w[(k - 1) * s]);
+    for (int k = 1; k < 16; ++k) {
+#if OLS_TW_GLOBAL
+        const float2 wk = __ldg(w + (k - 1) * s);
+#else
+        const float2 wk = w[(k - 1) * s];
+#endif
+        x[k] = ctw<INV>(x[k], wk);
+    }
 }
 
 template <int LOG2N, int P>
@@ -101,7 +128,7 @@ __device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const fl
     dft_groups<G::radix(P), false>(x);
     if constexpr (P < G::NP - 1) {
         twiddle<LOG2N, P, false>(x, tw, t);
-        exchange<LOG2N, P, P + 1>(x, bufs + (xc & 1) * G::PADN, t);
+        exchange<LOG2N, P, P + 1>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
         ++xc;
         forward_passes<LOG2N, P + 1>(x, bufs, tw, t, xc);
     }
@@ -113,7 +140,7 @@ template <int LOG2N, int P>
 __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {
     using G = Geo<LOG2N>;
     if constexpr (P < G::NP - 1) {
-        exchange<LOG2N, P + 1, P>(x, bufs + (xc & 1) * G::PADN, t);
+        exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
         ++xc;
         twiddle<LOG2N, P, true>(x, tw, t);
     }
@@ -121,21 +148,32 @@ __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const fl
     if constexpr (P > 0) inverse_passes<LOG2N, P - 1>(x, bufs, tw, t, xc);
 }
 
+__device__ __forceinline__ float4 load_spectrum(const float4 *p) {
+#if OLS_H_L2ONLY
+    return __ldcg(p);
+#else
+    return __ldg(p);
+#endif
+}
+
 template <int LOG2N>
-__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK)
+__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, Geo<LOG2N>::MINB)
 ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
                    const float2 *__restrict__ twg, float2 *__restrict__ y, int M, int F,
                    long long L, long long nseg, long long Nout) {
     using G = Geo<LOG2N>;
     extern __shared__ float4 smem_raw[];
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
-    float2 *tw = smem;
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
-    float2 *bufs = smem + G::TWN_PAD + slot * 2 * G::PADN;
-
+    float2 *bufs = smem + G::TWN_PAD + slot * G::XBUFS * G::PADN;
+#if OLS_TW_GLOBAL
+    const float2 *tw = twg;
+#else
+    float2 *tw = smem;
     for (int i = threadIdx.x; i < G::TWN; i += G::BLOCK) tw[i] = twg[i];
     __syncthreads();
+#endif
 
     const int lo = M - 1;                      // aliased samples per segment
     int xc = 0;
@@ -162,15 +200,33 @@ ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *_
         const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
         const long long obase = start - lo;
 
+#if OLS_PREFETCH_H
+        float4 hn[8];
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
+#endif
         for (int f = 0; f < F; ++f) {
             float2 x[16];
+#if OLS_PREFETCH_H
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) {
+                x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].y));
+                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
+            }
+            if (f + 1 < F) {
+                const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
+#pragma unroll
+                for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+            }
+#else
             const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2) {
-                const float4 h = __ldg(hp + j2 * G::T);
+                const float4 h = load_spectrum(hp + j2 * G::T);
                 x[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
                 x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
             }
+#endif
             inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
             float2 *dst = y + (size_t)f * (size_t)Nout;
 #pragma unroll
