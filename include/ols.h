@@ -159,8 +159,36 @@ OLS_API int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, 
 OLS_API int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y_host,
                       void *stream);
 
-/* Number of kernel launches the last ols_convolve on this plan enqueued
- * (for launch accounting in benchmarks). */
+/*
+ * Workspace (bytes) that ols_convolve_backward needs for a signal of Ns
+ * samples, given which gradients are wanted (want_ds, want_dh: 0 or 1).
+ * May be 0.  Errors: INVALID, UNSUPPORTED (as ols_geometry).
+ */
+OLS_API int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int want_dh, size_t *bytes);
+
+/*
+ * Adjoint of ols_convolve (the paper has no backward pass; this is derived
+ * from Eq. 1 by linearity, for training systems).  Gradient convention
+ * g = dL/dRe y + i dL/dIm y, g: device [F][Ns-M+1] complex.  Outputs:
+ *   ds[m]   = sum_f sum_k g_f[m-M+1+k] conj(h_f[k])          device [Ns] complex, or NULL
+ *   dh_f[k] = sum_j g_f[j] conj(s[j+M-1-k])                  device [F][M] complex, or NULL
+ * (at least one of them non-NULL; s may be NULL when dh is NULL).  Computed
+ * window by window in the frequency domain with the segment spectrum of s
+ * recomputed, 2F+2 on-chip FFTs per window, then a small finishing kernel
+ * (overlaps of ds, fixed-order compensated sum of the dh partials):
+ * deterministic for a given plan and device.  Outputs are overwritten, not
+ * accumulated.  workspace: device buffer of at least ols_backward_workspace()
+ * bytes, 256-byte aligned, owned by the caller; its contents on entry do not
+ * matter.  Errors: INVALID (pointers), NOT_READY, UNSUPPORTED (ds wanted with
+ * M-1 > N-M+1: choose N >= 2(M-1)), WORKSPACE (missing, small or misaligned),
+ * CUDA.
+ */
+OLS_API int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const float *g, float *ds,
+                                  float *dh, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Number of kernel launches the last compute call on this plan enqueued
+ * (ols_convolve, ols_convolve_host, ols_convolve_backward), for launch
+ * accounting in benchmarks. */
 OLS_API int ols_last_launch_count(ols_plan_t plan);
 
 #ifdef __cplusplus

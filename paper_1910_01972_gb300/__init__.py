@@ -15,7 +15,7 @@ import torch
 from . import _native
 from ._native import OLSError, check
 
-__all__ = ["Plan", "OLSError", "geometry", "spectrum_order", "convolve"]
+__all__ = ["Plan", "OLSError", "geometry", "spectrum_order", "convolve", "ols_conv"]
 
 
 def _stream_ptr(device) -> int:
@@ -134,6 +134,38 @@ class Plan:
                                         _stream_ptr(self.device)), "ols_convolve_host")
         return out_host
 
+    def backward_workspace(self, Ns: int, want_ds: bool = True, want_dh: bool = True) -> int:
+        rc, nb = _native.ols_backward_workspace(self._h, int(Ns), want_ds, want_dh)
+        check(rc, "ols_backward_workspace")
+        return nb
+
+    def convolve_backward(self, s: torch.Tensor | None, g: torch.Tensor, want_ds: bool = True,
+                          want_dh: bool = True, Ns: int | None = None):
+        """Adjoint of ``convolve``: returns (ds [Ns] or None, dh [F][M] or None).
+
+        g: [F][Ns-M+1] complex64, the gradient dL/dRe y + i dL/dIm y.
+        """
+        _require(g, "g", self.device)
+        if s is not None:
+            _require(s, "s", self.device)
+            Ns = s.shape[0]
+        if Ns is None:
+            raise ValueError("Ns is needed when s is not given")
+        if want_dh and s is None:
+            raise ValueError("dh needs the signal s")
+        if tuple(g.shape) != (self.F, Ns - self.M + 1):
+            raise ValueError("g must have shape [F][Ns-M+1]")
+        ds = torch.empty(Ns, dtype=torch.complex64, device=self.device) if want_ds else None
+        dh = torch.empty((self.F, self.M), dtype=torch.complex64, device=self.device) if want_dh else None
+        nb = self.backward_workspace(Ns, want_ds, want_dh)
+        ws = torch.empty(max(nb, 1) + 256, dtype=torch.uint8, device=self.device)
+        wp = (ws.data_ptr() + 255) & ~255
+        check(_native.ols_convolve_backward(self._h, s.data_ptr() if s is not None else None, Ns, g.data_ptr(),
+                                            ds.data_ptr() if ds is not None else None,
+                                            dh.data_ptr() if dh is not None else None, wp, nb,
+                                            _stream_ptr(self.device)), "ols_convolve_backward")
+        return ds, dh
+
     def last_launch_count(self) -> int:
         return _native.ols_last_launch_count(self._h)
 
@@ -148,3 +180,6 @@ def convolve(s: torch.Tensor, h: torch.Tensor, N: int = 0) -> torch.Tensor:
     torch.cuda.current_stream(plan.device).synchronize()
     plan.close()
     return y
+
+
+from .autograd import ols_conv  # noqa: E402  (needs Plan)

@@ -41,6 +41,8 @@ SIGNATURES = [
     ("ols_get_spectra", cint, [vp, vp, vp]),
     ("ols_convolve", cint, [vp, vp, i64, vp, vp]),
     ("ols_convolve_host", cint, [vp, vp, i64, vp, vp]),
+    ("ols_backward_workspace", cint, [vp, i64, cint, cint, ctypes.POINTER(ctypes.c_size_t)]),
+    ("ols_convolve_backward", cint, [vp, vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     ("ols_last_launch_count", cint, [vp]),
 ]
 
@@ -129,6 +131,17 @@ def ols_convolve(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
 
 def ols_convolve_host(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
     return lib().ols_convolve_host(plan, s_ptr, Ns, y_ptr, stream)
+
+
+def ols_backward_workspace(plan, Ns: int, want_ds: bool, want_dh: bool):
+    nb = ctypes.c_size_t()
+    rc = lib().ols_backward_workspace(plan, Ns, int(want_ds), int(want_dh), ctypes.byref(nb))
+    return rc, nb.value
+
+
+def ols_convolve_backward(plan, s_ptr, Ns: int, g_ptr: int, ds_ptr, dh_ptr, ws_ptr, ws_bytes: int,
+                          stream: int) -> int:
+    return lib().ols_convolve_backward(plan, s_ptr, Ns, g_ptr, ds_ptr, dh_ptr, ws_ptr, ws_bytes, stream)
 
 
 def ols_last_launch_count(plan) -> int:

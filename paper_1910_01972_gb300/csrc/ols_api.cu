@@ -103,6 +103,7 @@ static void free_staging(Staging &s) {
 static void free_plan(ols_plan_s *p) {
     if (!p) return;
     if (p->Hk) cudaFree(p->Hk);
+    if (p->Htk) cudaFree(p->Htk);
     if (p->tw) cudaFree(p->tw);
     if (p->tw64) cudaFree(p->tw64);
     if (p->nu) cudaFree(p->nu);
@@ -172,6 +173,7 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     if (e == cudaSuccess) e = cudaMalloc(&p->Hk, sizeof(float2) * (size_t)F * (size_t)N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->Htk, sizeof(float2) * (size_t)F * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&p->tw, sizeof(float2) * (size_t)(p->pp.twn > 0 ? p->pp.twn : 1));
     if (e == cudaSuccess) e = cudaMalloc(&p->tw64, sizeof(double2) * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&p->nu, sizeof(int32_t) * (size_t)N);
@@ -184,6 +186,7 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     }
     if (e == cudaSuccess) e = launch_tw64(p->tw64, (int)N, 0);
     if (e == cudaSuccess) e = prepare_forward(*p);
+    if (e == cudaSuccess) e = prepare_backward(*p);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_plan(p);
@@ -217,8 +220,12 @@ int ols_plan_query(ols_plan_t plan, int64_t Ns, int64_t *N, int32_t *M, int32_t 
 
 int ols_set_filters(ols_plan_t plan, const float *h, void *stream) {
     if (!plan || !h || !aligned8(h)) return OLS_ERR_INVALID;
-    cudaError_t e = launch_spectra(reinterpret_cast<const float2 *>(h), plan->M, plan->F, plan->log2N,
-                                   plan->nu, plan->tw64, plan->Hk, (cudaStream_t)stream);
+    const float2 *hh = reinterpret_cast<const float2 *>(h);
+    cudaError_t e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0,
+                                   (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Htk, 1,
+                           (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
     plan->filters_ready = true;
     return OLS_OK;
@@ -312,6 +319,62 @@ int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y
         cudaError_t e2 = cudaStreamSynchronize(st.st[i]);
         if (e == cudaSuccess) e = e2;
     }
+    plan->last_launches = launches;
+    return status_of(e);
+}
+
+// Workspace of the adjoint: overlap edges of ds (nseg x 2 x (M-1)), then the
+// per-slot dh partials (slots x F x M), each part 256-byte aligned.
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void backward_layout(const ols_plan_s &p, int64_t nseg, bool want_ds, bool want_dh, size_t *edge_bytes,
+                            size_t *part_bytes, int *grid, int *npart) {
+    *grid = backward_grid(p, nseg, want_ds, want_dh);
+    const int64_t slots = (int64_t)(*grid) * backward_segs_per_block(p.log2N);
+    *npart = (int)(slots < nseg ? slots : nseg);
+    *edge_bytes = want_ds ? align256(sizeof(float2) * (size_t)nseg * 2 * (size_t)(p.M - 1)) : 0;
+    *part_bytes = want_dh ? align256(sizeof(float2) * (size_t)slots * (size_t)p.F * (size_t)p.M) : 0;
+}
+
+int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int want_dh, size_t *bytes) {
+    if (!plan || !bytes) return OLS_ERR_INVALID;
+    int64_t L, nseg, Nout;
+    int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
+    if (rc != OLS_OK) return rc;
+    size_t eb, pb;
+    int grid, npart;
+    backward_layout(*plan, nseg, want_ds != 0, want_dh != 0, &eb, &pb, &grid, &npart);
+    *bytes = eb + pb;
+    return OLS_OK;
+}
+
+int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const float *g, float *ds, float *dh,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    if (!plan || !g || !aligned8(g) || (!ds && !dh)) return OLS_ERR_INVALID;
+    if ((ds && !aligned8(ds)) || (dh && !aligned8(dh))) return OLS_ERR_INVALID;
+    if (dh && (!s || !aligned8(s))) return OLS_ERR_INVALID;
+    if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    int64_t L, nseg, Nout;
+    int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
+    if (rc != OLS_OK) return rc;
+    if (ds && plan->M - 1 > L) return OLS_ERR_UNSUPPORTED;   // ds overlaps must span two windows at most
+    size_t eb, pb;
+    BackwardArgs a{};
+    backward_layout(*plan, nseg, ds != nullptr, dh != nullptr, &eb, &pb, &a.grid, &a.npart);
+    if (eb + pb > 0 && (!workspace || workspace_bytes < eb + pb || ((uintptr_t)workspace & 255u)))
+        return OLS_ERR_WORKSPACE;
+    a.s = reinterpret_cast<const float2 *>(s);
+    a.Ns = Ns;
+    a.g = reinterpret_cast<const float2 *>(g);
+    a.Nout = Nout;
+    a.L = L;
+    a.nseg = nseg;
+    a.ds = reinterpret_cast<float2 *>(ds);
+    a.dh = reinterpret_cast<float2 *>(dh);
+    a.edge = eb ? reinterpret_cast<float2 *>(workspace) : nullptr;
+    a.dh_part = pb ? reinterpret_cast<float2 *>(static_cast<char *>(workspace) + eb) : nullptr;
+    int launches = 0;
+    cudaError_t e = launch_backward(*plan, a, (cudaStream_t)stream, &launches);
     plan->last_launches = launches;
     return status_of(e);
 }

@@ -51,25 +51,43 @@ struct ols_plan_s {
     bool filters_ready = false;
     ols::PassPlan pp{};
     float2 *Hk = nullptr;        // [F][N] spectra in kernel layout (FP32)
+    float2 *Htk = nullptr;       // [F][N] spectra of conj(h_f[M-1-k]) (adjoint), kernel layout
     float2 *tw = nullptr;        // forward twiddles (FP32), pp.twn entries
     double2 *tw64 = nullptr;     // W_N^m, m in [0, N) (FP64)
     int32_t *nu = nullptr;       // spectral order (device copy)
     int fwd_grid_cap = 0;        // resident blocks of the forward kernel
+    int bwd_grid_cap[3] = {0, 0, 0};  // backward kernel: (ds,dh), (ds), (dh)
     int last_launches = 0;
     ols::Staging stage;
 };
 
 namespace ols {
 
+struct BackwardArgs {
+    const float2 *s;
+    int64_t Ns;
+    const float2 *g;
+    int64_t Nout, L, nseg;
+    float2 *ds, *dh;
+    float2 *edge, *dh_part;   // workspace parts
+    int grid, npart;
+};
+
 // Forward fused OLS (Algorithm 2).  Returns a cudaError_t.
 cudaError_t launch_forward(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y,
                            int64_t L, int64_t nseg, int64_t Nout, cudaStream_t st, int *launches);
 // Occupancy / attribute set-up of the forward kernel for p.log2N.
 cudaError_t prepare_forward(ols_plan_s &p);
-// FP64 precompute kernels.
+// Adjoint (ds, dh) of the fused OLS: the window kernel plus the finishing
+// kernel; `launches` receives the number of kernels enqueued.
+cudaError_t prepare_backward(ols_plan_s &p);
+cudaError_t launch_backward(const ols_plan_s &p, const BackwardArgs &a, cudaStream_t st, int *launches);
+int backward_grid(const ols_plan_s &p, int64_t nseg, bool want_ds, bool want_dh);
+int backward_segs_per_block(int log2N);
+// FP64 precompute kernels.  adjoint != 0 transforms conj(h_f[M-1-k]) instead of h_f[k].
 cudaError_t launch_tw64(double2 *tw64, int N, cudaStream_t st);
 cudaError_t launch_spectra(const float2 *h, int M, int F, int log2N, const int32_t *nu,
-                           const double2 *tw64, float2 *Hk, cudaStream_t st);
+                           const double2 *tw64, float2 *Hk, int adjoint, cudaStream_t st);
 cudaError_t launch_spectra_natural(const float2 *Hk, int F, int log2N, const int32_t *nu,
                                    float2 *H, cudaStream_t st);
 

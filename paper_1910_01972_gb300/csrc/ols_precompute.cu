@@ -25,9 +25,11 @@ __global__ void tw64_kernel(double2 *tw64, int N) {
 // q (nu = nu_tab[q]) in the kernel's register layout: thread t = q / 16 holds
 // register j = q % 16, and registers (2i, 2i+1) of all threads of a segment
 // are interleaved so one 16-byte load fetches a pair.
+// With adjoint != 0 the transformed filter is conj(h_f[M-1-k]) (the adjoint
+// of the convolution correlates with h).
 __global__ void spectra_kernel(const float2 *__restrict__ h, int M, int F, int log2N,
                                const int32_t *__restrict__ nu_tab, const double2 *__restrict__ tw64,
-                               float2 *__restrict__ Hk) {
+                               float2 *__restrict__ Hk, int adjoint) {
     const int N = 1 << log2N;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)F * N) return;
@@ -38,7 +40,8 @@ __global__ void spectra_kernel(const float2 *__restrict__ h, int M, int F, int l
     double ar = 0.0, ai = 0.0;
     for (int k = 0; k < M; ++k) {
         const double2 w = tw64[(nu * k) & (N - 1)];
-        const float2 hk = hf[k];
+        float2 hk = hf[adjoint ? (M - 1 - k) : k];
+        if (adjoint) hk.y = -hk.y;
         ar = fma((double)hk.x, w.x, fma(-(double)hk.y, w.y, ar));
         ai = fma((double)hk.x, w.y, fma((double)hk.y, w.x, ai));
     }
@@ -67,9 +70,9 @@ cudaError_t launch_tw64(double2 *tw64, int N, cudaStream_t st) {
 }
 
 cudaError_t launch_spectra(const float2 *h, int M, int F, int log2N, const int32_t *nu,
-                           const double2 *tw64, float2 *Hk, cudaStream_t st) {
+                           const double2 *tw64, float2 *Hk, int adjoint, cudaStream_t st) {
     const long long total = (long long)F << log2N;
-    spectra_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(h, M, F, log2N, nu, tw64, Hk);
+    spectra_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(h, M, F, log2N, nu, tw64, Hk, adjoint);
     return cudaGetLastError();
 }
 
