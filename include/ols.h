@@ -58,7 +58,8 @@ typedef enum {
     OLS_ERR_CUDA = 4,         /* a CUDA runtime call failed (including: no device) */
     OLS_ERR_NOT_READY = 5,    /* filters were not set on the plan */
     OLS_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
-    OLS_ERR_WORKSPACE = 7     /* caller workspace missing or too small */
+    OLS_ERR_WORKSPACE = 7,    /* caller workspace missing or too small */
+    OLS_ERR_TOO_LARGE = 8     /* problem needs more than a fixed built-in limit */
 } ols_status;
 
 typedef struct ols_plan_s *ols_plan_t;
@@ -185,6 +186,34 @@ OLS_API int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int
  */
 OLS_API int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const float *g, float *ds,
                                   float *dh, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Size in bytes of the scratch array built into the library for
+ * ols_convolve_backward_noalloc. */
+#define OLS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * ols_convolve_backward without a caller workspace and without allocating
+ * (the paper has no counterpart: this serves callers that cannot allocate
+ * device memory -- real-time pipelines that forbid allocation once running,
+ * since cudaMalloc can block and synchronise the device, and hosts that own
+ * every device allocation themselves).  Same arguments, results and errors
+ * as ols_convolve_backward minus the workspace; the scratch is a fixed
+ * device array of OLS_NOALLOC_SCRATCH_BYTES inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ * - Problems whose ols_backward_workspace() exceeds that size are rejected
+ *   with OLS_ERR_TOO_LARGE before any work is enqueued.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with the plan's device current); make that first
+ *   call before any stream capture.  The plan's device must be current
+ *   (else OLS_ERR_INVALID).  No cudaMalloc, cudaFree or other allocating
+ *   routine is called.
+ * - Every call on a device shares the one array, which keeps the last call's
+ *   contents (nothing in it needs to start at zero).  Calls that overlap on
+ *   the GPU -- other streams, other threads, other plans -- race on it:
+ *   serialise them.
+ */
+OLS_API int ols_convolve_backward_noalloc(ols_plan_t plan, const float *s, int64_t Ns, const float *g, float *ds,
+                                          float *dh, void *stream);
 
 /* Number of kernel launches the last compute call on this plan enqueued
  * (ols_convolve, ols_convolve_host, ols_convolve_backward), for launch

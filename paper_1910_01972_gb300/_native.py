@@ -22,6 +22,8 @@ OLS_ERR_CUDA = 4
 OLS_ERR_NOT_READY = 5
 OLS_ERR_TIMEOUT = 6
 OLS_ERR_WORKSPACE = 7
+OLS_ERR_TOO_LARGE = 8
+OLS_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 OLS_FLAG_FP32 = 0
 
@@ -43,6 +45,7 @@ SIGNATURES = [
     ("ols_convolve_host", cint, [vp, vp, i64, vp, vp]),
     ("ols_backward_workspace", cint, [vp, i64, cint, cint, ctypes.POINTER(ctypes.c_size_t)]),
     ("ols_convolve_backward", cint, [vp, vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+    ("ols_convolve_backward_noalloc", cint, [vp, vp, i64, vp, vp, vp, vp]),
     ("ols_last_launch_count", cint, [vp]),
 ]
 
@@ -142,6 +145,10 @@ def ols_backward_workspace(plan, Ns: int, want_ds: bool, want_dh: bool):
 def ols_convolve_backward(plan, s_ptr, Ns: int, g_ptr: int, ds_ptr, dh_ptr, ws_ptr, ws_bytes: int,
                           stream: int) -> int:
     return lib().ols_convolve_backward(plan, s_ptr, Ns, g_ptr, ds_ptr, dh_ptr, ws_ptr, ws_bytes, stream)
+
+
+def ols_convolve_backward_noalloc(plan, s_ptr, Ns: int, g_ptr: int, ds_ptr, dh_ptr, stream: int) -> int:
+    return lib().ols_convolve_backward_noalloc(plan, s_ptr, Ns, g_ptr, ds_ptr, dh_ptr, stream)
 
 
 def ols_last_launch_count(plan) -> int:

@@ -127,6 +127,7 @@ const char *ols_status_string(int status) {
         case OLS_ERR_NOT_READY: return "OLS_ERR_NOT_READY: filters not set";
         case OLS_ERR_TIMEOUT: return "OLS_ERR_TIMEOUT: bounded device wait gave up";
         case OLS_ERR_WORKSPACE: return "OLS_ERR_WORKSPACE: workspace missing or too small";
+        case OLS_ERR_TOO_LARGE: return "OLS_ERR_TOO_LARGE: problem exceeds the built-in scratch size";
         default: return "OLS_ERR_UNKNOWN";
     }
 }

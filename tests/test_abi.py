@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 
 def test_status_strings():
-    for st in range(0, 8):
+    for st in range(0, 9):
         assert _native.ols_status_string(st).startswith("OLS_")
     assert _native.ols_version() >= 100
 
