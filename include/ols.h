@@ -63,6 +63,7 @@ typedef enum {
 } ols_status;
 
 typedef struct ols_plan_s *ols_plan_t;
+typedef struct ols_batch_s *ols_batch_t;
 
 /* Plan flags (arithmetic of the plain convolution). */
 #define OLS_FLAG_FP32 0u
@@ -186,6 +187,67 @@ OLS_API int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int
  */
 OLS_API int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const float *g, float *ds,
                                   float *dh, void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Segment-length autotuner and the batched form.
+ * Sec. 5 of the paper observes that each segment length is the fastest for
+ * a range of filter lengths only (a longer segment wastes a smaller
+ * fraction M-1 of each FFT but costs more per point); the autotuner measures
+ * that trade-off on the device instead of fixing N.
+ * --------------------------------------------------------------------- */
+
+/* Autotuner flag: use the cost model (N/L)(log2 N + c) instead of timing. */
+#define OLS_TUNE_MODEL (1u << 8)
+
+/*
+ * Pick the segment length N in {256, ..., 8192} (N >= M) for M taps and F
+ * filters: with flags = 0 the fused kernel is timed on the current device for
+ * every candidate on a zero signal of about two waves of segments (allocates
+ * up to ~256 MB of temporary device memory, synchronises the device) and the
+ * fastest per output sample wins; results are cached per (M, F) for the
+ * process and, if the environment variable OLS_AUTOTUNE_CACHE names a file,
+ * read from and appended to it ("M F N" lines).  With OLS_TUNE_MODEL, no
+ * measurement.  Errors: INVALID, UNSUPPORTED (M > 8192), CUDA.
+ */
+OLS_API int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N);
+
+/*
+ * A batch of B independent problems of uneven size: signal b has Ns[b]
+ * samples, F[b] filters of M[b] taps, segment length N[b] (N == NULL or
+ * N[b] == 0: ols_autotune(M[b], F[b], flags)).  Host arrays of B entries.
+ * Problems sharing a segment length form one persistent launch whose
+ * resident blocks pull (problem, segment tile) work items from an atomic
+ * ticket, most filters first; every segment is computed exactly as by
+ * ols_convolve on the same N, so results are identical to per-problem calls.
+ * Allocates per-problem spectra and the work tables.
+ * Errors: INVALID (B < 1, NULL arrays, an Ns < M, M < 1, F < 1), UNSUPPORTED,
+ * ALLOC, CUDA.
+ */
+OLS_API int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t *M, const int32_t *F,
+                           const int64_t *N, uint32_t flags);
+OLS_API int ols_batch_destroy(ols_batch_t batch);
+
+/* Segment length and output length of problem b, and the number of
+ * persistent launches (distinct segment lengths) per call.  Any output
+ * pointer may be NULL.  Errors: INVALID. */
+OLS_API int ols_batch_query(ols_batch_t batch, int32_t b, int64_t *N, int64_t *Nout, int32_t *ngroups);
+
+/* Filter spectra of every problem (as ols_set_filters): h is a HOST array of
+ * B device pointers, h[b] -> [F[b]][M[b]] complex.  Errors: INVALID, CUDA. */
+OLS_API int ols_batch_set_filters(ols_batch_t batch, const float *const *h, void *stream);
+
+/*
+ * Convolve every problem: s_ptrs and y_ptrs are DEVICE arrays of B device
+ * pointers (s_ptrs[b] -> [Ns[b]] complex, y_ptrs[b] -> [F[b]][Ns[b]-M[b]+1]
+ * complex), read by the kernels, so the call enqueues only a memset of the
+ * tickets and one launch per segment length: it can be captured in a CUDA
+ * graph and replayed with new data behind the same pointers.
+ * Errors: INVALID, NOT_READY, CUDA.
+ */
+OLS_API int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_ptrs, void *stream);
+
+/* Kernel launches enqueued by the last ols_convolve_batched. */
+OLS_API int ols_batch_last_launch_count(ols_batch_t batch);
 
 /* Size in bytes of the scratch array built into the library for
  * ols_convolve_backward_noalloc. */

@@ -15,7 +15,7 @@ import torch
 from . import _native
 from ._native import OLSError, check
 
-__all__ = ["Plan", "OLSError", "geometry", "spectrum_order", "convolve", "ols_conv"]
+__all__ = ["Plan", "BatchPlan", "OLSError", "geometry", "spectrum_order", "convolve", "ols_conv", "autotune"]
 
 
 def _stream_ptr(device) -> int:
@@ -168,6 +168,95 @@ class Plan:
 
     def last_launch_count(self) -> int:
         return _native.ols_last_launch_count(self._h)
+
+
+def autotune(M: int, F: int, model_only: bool = False) -> int:
+    """Segment length the library picks for M taps and F filters (timed on the
+    current device unless model_only)."""
+    rc, n = _native.ols_autotune(int(M), int(F), _native.OLS_TUNE_MODEL if model_only else 0)
+    check(rc, "ols_autotune")
+    return n
+
+
+class BatchPlan:
+    """B independent problems of uneven size (Ns[b], M[b], F[b], N[b]; N None
+    or 0 entries are autotuned), convolved by one persistent launch per
+    distinct segment length."""
+
+    def __init__(self, Ns, M, F, N=None, model_only: bool = False):
+        rc, handle = _native.ols_batch_plan(list(Ns), list(M), list(F), None if N is None else list(N),
+                                            _native.OLS_TUNE_MODEL if model_only else 0)
+        check(rc, "ols_batch_plan")
+        self._h = handle
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.B = len(Ns)
+        self.Ns, self.M, self.F = list(Ns), list(M), list(F)
+        self.N, self.Nout = [], []
+        for b in range(self.B):
+            rc, n, nout, ng = _native.ols_batch_query(self._h, b)
+            check(rc, "ols_batch_query")
+            self.N.append(n)
+            self.Nout.append(nout)
+            self.ngroups = ng
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.ols_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def set_filters(self, hs) -> None:
+        """hs: list of B device tensors [F[b]][M[b]] complex64."""
+        for b, h in enumerate(hs):
+            _require(h, "h[%d]" % b, self.device)
+            if tuple(h.shape) != (self.F[b], self.M[b]):
+                raise ValueError("h[%d] must have shape [%d][%d]" % (b, self.F[b], self.M[b]))
+        check(_native.ols_batch_set_filters(self._h, [h.data_ptr() for h in hs], _stream_ptr(self.device)),
+              "ols_batch_set_filters")
+        self._keep = list(hs)
+
+    def outputs(self):
+        """Freshly allocated outputs [F[b]][Nout[b]] for every problem."""
+        return [torch.empty((f, n), dtype=torch.complex64, device=self.device) for f, n in zip(self.F, self.Nout)]
+
+    def pointer_table(self, tensors) -> torch.Tensor:
+        """Device int64 table of the tensors' data pointers (what the kernels read)."""
+        return torch.tensor([t.data_ptr() for t in tensors], dtype=torch.int64, device=self.device)
+
+    def launch(self, s_table: torch.Tensor, y_table: torch.Tensor) -> None:
+        """Enqueue the batched convolution for pointer tables already on the
+        device (graph-capturable: no allocation, no host synchronisation)."""
+        check(_native.ols_convolve_batched(self._h, s_table.data_ptr(), y_table.data_ptr(),
+                                           _stream_ptr(self.device)), "ols_convolve_batched")
+
+    def convolve(self, ss, ys=None):
+        """ss: list of B device tensors [Ns[b]]; returns the list of outputs."""
+        for b, s in enumerate(ss):
+            _require(s, "s[%d]" % b, self.device)
+            if s.shape != (self.Ns[b],):
+                raise ValueError("s[%d] must have %d samples" % (b, self.Ns[b]))
+        if ys is None:
+            ys = self.outputs()
+        for b, y in enumerate(ys):
+            _require(y, "y[%d]" % b, self.device)
+            if tuple(y.shape) != (self.F[b], self.Nout[b]):
+                raise ValueError("y[%d] has the wrong shape" % b)
+        st, yt = self.pointer_table(ss), self.pointer_table(ys)
+        self.launch(st, yt)
+        return ys
+
+    def last_launch_count(self) -> int:
+        return _native.ols_batch_last_launch_count(self._h)
 
 
 def convolve(s: torch.Tensor, h: torch.Tensor, N: int = 0) -> torch.Tensor:

@@ -26,6 +26,7 @@ OLS_ERR_TOO_LARGE = 8
 OLS_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 OLS_FLAG_FP32 = 0
+OLS_TUNE_MODEL = 1 << 8
 
 # (name, restype, argtypes) of every exported symbol declared in include/ols.h
 i32, i64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
@@ -47,6 +48,13 @@ SIGNATURES = [
     ("ols_convolve_backward", cint, [vp, vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     ("ols_convolve_backward_noalloc", cint, [vp, vp, i64, vp, vp, vp, vp]),
     ("ols_last_launch_count", cint, [vp]),
+    ("ols_autotune", cint, [i32, i32, u32, P_i64]),
+    ("ols_batch_plan", cint, [ctypes.POINTER(vp), i32, P_i64, P_i32, P_i32, P_i64, u32]),
+    ("ols_batch_destroy", cint, [vp]),
+    ("ols_batch_query", cint, [vp, i32, P_i64, P_i64, P_i32]),
+    ("ols_batch_set_filters", cint, [vp, ctypes.POINTER(vp), vp]),
+    ("ols_convolve_batched", cint, [vp, vp, vp, vp]),
+    ("ols_batch_last_launch_count", cint, [vp]),
 ]
 
 _lib = None
@@ -153,3 +161,43 @@ def ols_convolve_backward_noalloc(plan, s_ptr, Ns: int, g_ptr: int, ds_ptr, dh_p
 
 def ols_last_launch_count(plan) -> int:
     return lib().ols_last_launch_count(plan)
+
+
+def ols_autotune(M: int, F: int, flags: int = 0):
+    n = i64()
+    rc = lib().ols_autotune(M, F, flags, ctypes.byref(n))
+    return rc, n.value
+
+
+def ols_batch_plan(Ns, M, F, N=None, flags: int = 0):
+    B = len(Ns)
+    a_ns = (i64 * B)(*Ns)
+    a_m = (i32 * B)(*M)
+    a_f = (i32 * B)(*F)
+    a_n = (i64 * B)(*N) if N is not None else None
+    h = vp()
+    rc = lib().ols_batch_plan(ctypes.byref(h), B, a_ns, a_m, a_f, a_n, flags)
+    return rc, h.value
+
+
+def ols_batch_destroy(batch) -> int:
+    return lib().ols_batch_destroy(batch)
+
+
+def ols_batch_query(batch, b: int):
+    N, Nout, ng = i64(), i64(), i32()
+    rc = lib().ols_batch_query(batch, b, ctypes.byref(N), ctypes.byref(Nout), ctypes.byref(ng))
+    return rc, N.value, Nout.value, ng.value
+
+
+def ols_batch_set_filters(batch, h_ptrs, stream: int) -> int:
+    arr = (vp * len(h_ptrs))(*h_ptrs)
+    return lib().ols_batch_set_filters(batch, arr, stream)
+
+
+def ols_convolve_batched(batch, s_ptrs_dev: int, y_ptrs_dev: int, stream: int) -> int:
+    return lib().ols_convolve_batched(batch, s_ptrs_dev, y_ptrs_dev, stream)
+
+
+def ols_batch_last_launch_count(batch) -> int:
+    return lib().ols_batch_last_launch_count(batch)

@@ -69,7 +69,7 @@ static int status_of(cudaError_t e) {
 // Segment-length rule (Sec. 3.2 and Sec. 5): a longer segment wastes a
 // smaller fraction M-1 of each FFT but costs log2(N) per point; pick the N
 // minimising the work per valid output, (N / L) (log2 N + c).
-static int64_t choose_N(int32_t M) {
+int64_t choose_segment_length(int32_t M) {
     double best = 1e300;
     int64_t bestN = 0;
     for (int l = kMinLog2N; l <= kMaxLog2N; ++l) {
@@ -159,7 +159,7 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     *out = nullptr;
     if (M < 1 || F < 1) return OLS_ERR_INVALID;
     if (flags != OLS_FLAG_FP32) return OLS_ERR_UNSUPPORTED;
-    if (N == 0) N = choose_N(M);
+    if (N == 0) N = choose_segment_length(M);
     const int l = log2_exact(N);
     if (l < kMinLog2N || l > kMaxLog2N || M > N) return OLS_ERR_UNSUPPORTED;
 

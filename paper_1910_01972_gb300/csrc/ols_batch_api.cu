@@ -1,0 +1,328 @@
+// ols_batch_api.cu -- C ABI of the batched form and the segment-length
+// autotuner (include/ols.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "ols.h"
+#include "ols_internal.h"
+
+struct ols_batch_s {
+    int device = 0;
+    int sm_count = 0;
+    int B = 0;
+    std::vector<ols_plan_t> plans;            // one plain plan per problem (spectra, twiddles)
+    std::vector<int64_t> Ns, Nout, N, L, nseg;
+    std::vector<int32_t> M, F;
+    std::vector<ols::BatchGroup> groups;
+    ols::BatchProblemDev *d_probs = nullptr;
+    int2 *d_items = nullptr;
+    unsigned long long *d_tickets = nullptr;
+    bool filters_ready = false;
+    int last_launches = 0;
+};
+
+namespace {
+
+using namespace ols;
+
+int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return OLS_OK;
+    if (e == cudaErrorMemoryAllocation) return OLS_ERR_ALLOC;
+    return OLS_ERR_CUDA;
+}
+
+int log2_of(int64_t N) {
+    if (N <= 0 || (N & (N - 1))) return -1;
+    int l = 0;
+    while ((int64_t(1) << l) < N) ++l;
+    return l;
+}
+
+// ---------------------------------------------------------------- autotuner
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int64_t> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+void load_tune_file_locked() {
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char *path = std::getenv("OLS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *fh = std::fopen(path, "r");
+    if (!fh) return;
+    int m, f;
+    long long n;
+    while (std::fscanf(fh, "%d %d %lld", &m, &f, &n) == 3) {
+        const int l = log2_of(n);
+        if (m >= 1 && f >= 1 && l >= kMinLog2N && l <= kMaxLog2N && m <= n) g_tune_cache[{m, f}] = n;
+    }
+    std::fclose(fh);
+}
+
+void store_tune_file_locked(int M, int F, int64_t N) {
+    const char *path = std::getenv("OLS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *fh = std::fopen(path, "a");
+    if (!fh) return;
+    std::fprintf(fh, "%d %d %lld\n", M, F, (long long)N);
+    std::fclose(fh);
+}
+
+// Device time per output sample of the fused kernel for (N, M, F), on a
+// zero signal of about two waves of segments (timing does not depend on the
+// values).  Returns a negative value on failure.
+double measure_per_output(int64_t N, int32_t M, int32_t F) {
+    ols_plan_t p = nullptr;
+    if (ols_plan(&p, N, M, F, OLS_FLAG_FP32) != OLS_OK) return -1.0;
+    double result = -1.0;
+    float2 *h = nullptr, *s = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int64_t L = N - M + 1;
+    int64_t nseg = 2ll * p->fwd_grid_cap * 8;
+    const int64_t max_out = (256ll << 20) / (8ll * F);          // <= 256 MB of output
+    if (nseg * L > max_out) nseg = std::max<int64_t>(1, max_out / L);
+    const int64_t Nout = nseg * L, Ns = Nout + M - 1;
+    cudaError_t e = cudaMalloc(&h, sizeof(float2) * (size_t)F * M);
+    if (e == cudaSuccess) e = cudaMalloc(&s, sizeof(float2) * (size_t)Ns);
+    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(float2) * (size_t)F * Nout);
+    if (e == cudaSuccess) e = cudaMemset(h, 0, sizeof(float2) * (size_t)F * M);
+    if (e == cudaSuccess) e = cudaMemset(s, 0, sizeof(float2) * (size_t)Ns);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && ols_set_filters(p, reinterpret_cast<float *>(h), nullptr) == OLS_OK) {
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w)
+            ok = ols_convolve(p, reinterpret_cast<float *>(s), Ns, reinterpret_cast<float *>(y), nullptr) == OLS_OK;
+        float best = 1e30f;
+        for (int r = 0; r < 3 && ok; ++r) {
+            cudaEventRecord(e0, nullptr);
+            ok = ols_convolve(p, reinterpret_cast<float *>(s), Ns, reinterpret_cast<float *>(y), nullptr) == OLS_OK;
+            cudaEventRecord(e1, nullptr);
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::min(best, ms);
+            } else {
+                ok = false;
+            }
+        }
+        if (ok) result = (double)best * 1e-3 / (double)(F * Nout);
+    }
+    cudaDeviceSynchronize();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (h) cudaFree(h);
+    if (s) cudaFree(s);
+    if (y) cudaFree(y);
+    ols_plan_destroy(p);
+    return result;
+}
+
+void free_batch(ols_batch_s *b) {
+    if (!b) return;
+    for (ols_plan_t p : b->plans)
+        if (p) ols_plan_destroy(p);
+    if (b->d_probs) cudaFree(b->d_probs);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_tickets) cudaFree(b->d_tickets);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N) {
+    if (!N || M < 1 || F < 1) return OLS_ERR_INVALID;
+    if (M > (1 << kMaxLog2N)) return OLS_ERR_UNSUPPORTED;
+    if (flags & OLS_TUNE_MODEL) {
+        *N = ols::choose_segment_length(M);
+        return OLS_OK;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    load_tune_file_locked();
+    auto it = g_tune_cache.find({M, F});
+    if (it != g_tune_cache.end()) {
+        *N = it->second;
+        return OLS_OK;
+    }
+    double best = 1e300;
+    int64_t bestN = 0;
+    for (int l = kMinLog2N; l <= kMaxLog2N; ++l) {
+        const int64_t n = int64_t(1) << l;
+        if (M > n) continue;
+        if ((n - M + 1) * 16 < n && n != (int64_t(1) << kMaxLog2N)) continue;   // < 1/16 of each FFT kept
+        const double t = measure_per_output(n, M, F);
+        if (t < 0) return OLS_ERR_CUDA;
+        if (t < best) {
+            best = t;
+            bestN = n;
+        }
+    }
+    if (bestN == 0) return OLS_ERR_UNSUPPORTED;
+    g_tune_cache[{M, F}] = bestN;
+    store_tune_file_locked(M, F, bestN);
+    *N = bestN;
+    return OLS_OK;
+}
+
+int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t *M, const int32_t *F,
+                   const int64_t *N, uint32_t flags) {
+    if (!out) return OLS_ERR_INVALID;
+    *out = nullptr;
+    if (B < 1 || !Ns || !M || !F) return OLS_ERR_INVALID;
+    for (int b = 0; b < B; ++b)
+        if (M[b] < 1 || F[b] < 1 || Ns[b] < M[b]) return OLS_ERR_INVALID;
+    ols_batch_s *bt = new (std::nothrow) ols_batch_s();
+    if (!bt) return OLS_ERR_ALLOC;
+    bt->B = B;
+    cudaError_t e = cudaGetDevice(&bt->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&bt->sm_count, cudaDevAttrMultiProcessorCount, bt->device);
+    if (e != cudaSuccess) {
+        free_batch(bt);
+        return status_of(e);
+    }
+    bt->plans.assign(B, nullptr);
+    bt->Ns.assign(Ns, Ns + B);
+    bt->M.assign(M, M + B);
+    bt->F.assign(F, F + B);
+    bt->N.resize(B);
+    bt->Nout.resize(B);
+    bt->L.resize(B);
+    bt->nseg.resize(B);
+    for (int b = 0; b < B; ++b) {
+        int64_t n = N ? N[b] : 0;
+        if (n == 0) {
+            int rc = ols_autotune(M[b], F[b], flags, &n);
+            if (rc != OLS_OK) {
+                free_batch(bt);
+                return rc;
+            }
+        }
+        int rc = ols_plan(&bt->plans[b], n, M[b], F[b], OLS_FLAG_FP32);
+        if (rc == OLS_OK) rc = ols_geometry(n, M[b], Ns[b], &bt->L[b], &bt->nseg[b], &bt->Nout[b]);
+        if (rc != OLS_OK) {
+            free_batch(bt);
+            return rc;
+        }
+        bt->N[b] = n;
+    }
+    // groups by segment length; problems in a group by decreasing F
+    std::vector<int> order(B);
+    for (int b = 0; b < B; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        if (bt->N[a] != bt->N[c]) return bt->N[a] < bt->N[c];
+        return bt->F[a] > bt->F[c];
+    });
+    std::vector<BatchProblemDev> probs;
+    std::vector<int2> items;
+    std::vector<std::pair<size_t, size_t>> ranges;   // per group: probs begin, items begin
+    for (size_t i = 0; i < order.size();) {
+        const int l = log2_of(bt->N[order[i]]);
+        BatchGroup g;
+        g.log2N = l;
+        int cap = 0, segs = 1;
+        e = batched_prepare(l, bt->sm_count, &cap, &segs);
+        if (e != cudaSuccess) {
+            free_batch(bt);
+            return status_of(e);
+        }
+        const size_t p0 = probs.size(), i0 = items.size();
+        size_t j = i;
+        for (; j < order.size() && bt->N[order[j]] == bt->N[order[i]]; ++j) {
+            const int b = order[j];
+            BatchProblemDev d{};
+            d.Hk = reinterpret_cast<const float4 *>(bt->plans[b]->Hk);
+            d.Ns = bt->Ns[b];
+            d.Nout = bt->Nout[b];
+            d.L = bt->L[b];
+            d.nseg = bt->nseg[b];
+            d.M = bt->M[b];
+            d.F = bt->F[b];
+            d.index = b;
+            const int pi = (int)(probs.size() - p0);
+            probs.push_back(d);
+            const int64_t tiles = (bt->nseg[b] + segs - 1) / segs;
+            for (int64_t tl = 0; tl < tiles; ++tl) items.push_back(make_int2(pi, (int)tl));
+        }
+        g.nitems = (long long)(items.size() - i0);
+        g.grid = (int)std::min<long long>(g.nitems, cap);
+        g.tw = bt->plans[order[i]]->tw;
+        bt->groups.push_back(g);
+        ranges.push_back({p0, i0});
+        i = j;
+    }
+    const size_t ng = bt->groups.size();
+    e = cudaMalloc(&bt->d_probs, sizeof(BatchProblemDev) * probs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_tickets, sizeof(unsigned long long) * ng);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(bt->d_probs, probs.data(), sizeof(BatchProblemDev) * probs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(bt->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_batch(bt);
+        return status_of(e);
+    }
+    for (size_t gi = 0; gi < ng; ++gi) {
+        bt->groups[gi].probs = bt->d_probs + ranges[gi].first;
+        bt->groups[gi].items = bt->d_items + ranges[gi].second;
+        bt->groups[gi].ticket = bt->d_tickets + gi;
+    }
+    *out = bt;
+    return OLS_OK;
+}
+
+int ols_batch_destroy(ols_batch_t batch) {
+    if (!batch) return OLS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_batch(batch);
+    return status_of(e);
+}
+
+int ols_batch_query(ols_batch_t batch, int32_t b, int64_t *N, int64_t *Nout, int32_t *ngroups) {
+    if (!batch || b < 0 || b >= batch->B) return OLS_ERR_INVALID;
+    if (N) *N = batch->N[b];
+    if (Nout) *Nout = batch->Nout[b];
+    if (ngroups) *ngroups = (int32_t)batch->groups.size();
+    return OLS_OK;
+}
+
+int ols_batch_set_filters(ols_batch_t batch, const float *const *h, void *stream) {
+    if (!batch || !h) return OLS_ERR_INVALID;
+    for (int b = 0; b < batch->B; ++b) {
+        const int rc = ols_set_filters(batch->plans[b], h[b], stream);
+        if (rc != OLS_OK) return rc;
+    }
+    batch->filters_ready = true;
+    return OLS_OK;
+}
+
+int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_ptrs, void *stream) {
+    if (!batch || !s_ptrs || !y_ptrs) return OLS_ERR_INVALID;
+    if (((uintptr_t)s_ptrs & 7u) || ((uintptr_t)y_ptrs & 7u)) return OLS_ERR_INVALID;
+    if (!batch->filters_ready) return OLS_ERR_NOT_READY;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(batch->d_tickets, 0, sizeof(unsigned long long) * batch->groups.size(), st);
+    int launches = 0;
+    for (size_t gi = 0; gi < batch->groups.size() && e == cudaSuccess; ++gi) {
+        e = batched_launch(batch->groups[gi], static_cast<const float2 *const *>(s_ptrs),
+                           static_cast<float2 *const *>(y_ptrs), st);
+        if (e == cudaSuccess) ++launches;
+    }
+    batch->last_launches = launches;
+    return status_of(e);
+}
+
+int ols_batch_last_launch_count(ols_batch_t batch) { return batch ? batch->last_launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// ols_batched.cu -- many OLS problems of uneven size in persistent launches.
+//
+// A batch holds B independent problems (signal b of Ns_b samples, F_b
+// filters of M_b taps, segment length N_b).  Problems that share N form a
+// group; each group is one persistent launch of the fused kernel whose
+// resident blocks pull work items -- a tile of Geo<>::SEGS consecutive
+// segments of one problem -- from an atomic ticket until the group's item
+// list is exhausted.  Items are ordered by decreasing filter count (the
+// most expensive first) so the dynamic schedule ends with short items.  Each
+// segment is processed exactly as by the plain kernel (ols_segment), so a
+// batched result equals the single-problem result bit for bit.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ols_internal.h"
+#include "ols_segment.cuh"
+
+namespace ols {
+
+template <int LOG2N>
+__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, Geo<LOG2N>::MINB)
+ols_batched_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__restrict__ items, long long nitems,
+                   const float2 *const *__restrict__ s_ptrs, float2 *const *__restrict__ y_ptrs,
+                   unsigned long long *__restrict__ ticket, const float2 *__restrict__ twg) {
+    using G = Geo<LOG2N>;
+    extern __shared__ float4 smem_raw[];
+    __shared__ long long item_sh;
+    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+    const int slot = threadIdx.x / G::T;
+    const int t = threadIdx.x % G::T;
+    float2 *bufs = smem + G::TWN_PAD + slot * G::XBUFS * G::PADN;
+#if OLS_TW_GLOBAL
+    const float2 *tw = twg;
+#else
+    float2 *tw = smem;
+    for (int i = threadIdx.x; i < G::TWN; i += G::BLOCK) tw[i] = twg[i];
+#endif
+    int xc = 0;
+    for (;;) {
+        __syncthreads();                       // previous item_sh readers are done
+        if (threadIdx.x == 0) item_sh = (long long)atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const long long item = item_sh;
+        if (item >= nitems) break;
+        const int2 it = items[item];           // (problem, tile)
+        const BatchProblemDev P = probs[it.x];
+        const long long nseg = P.nseg;
+        const long long seg = (long long)it.y * G::SEGS + slot;
+        ols_segment<LOG2N>(s_ptrs[P.index], P.Ns, P.Hk, tw, y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
+                           seg < nseg, bufs, t, xc);
+    }
+}
+
+template <int LOG2N>
+static cudaError_t batched_prepare_n(int sm_count, int *grid_cap, int *segs) {
+    using G = Geo<LOG2N>;
+    cudaError_t e = cudaFuncSetAttribute(ols_batched_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_kernel<LOG2N>, G::BLOCK, G::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *grid_cap = per_sm * sm_count;
+    *segs = G::SEGS;
+    return cudaSuccess;
+}
+
+cudaError_t batched_prepare(int log2N, int sm_count, int *grid_cap, int *segs) {
+    switch (log2N) {
+        case 8: return batched_prepare_n<8>(sm_count, grid_cap, segs);
+        case 9: return batched_prepare_n<9>(sm_count, grid_cap, segs);
+        case 10: return batched_prepare_n<10>(sm_count, grid_cap, segs);
+        case 11: return batched_prepare_n<11>(sm_count, grid_cap, segs);
+        case 12: return batched_prepare_n<12>(sm_count, grid_cap, segs);
+        case 13: return batched_prepare_n<13>(sm_count, grid_cap, segs);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LOG2N>
+static void batched_launch_n(const BatchGroup &g, const float2 *const *s_ptrs, float2 *const *y_ptrs,
+                             cudaStream_t st) {
+    using G = Geo<LOG2N>;
+    ols_batched_kernel<LOG2N><<<g.grid, G::BLOCK, G::SMEM, st>>>(g.probs, g.items, g.nitems, s_ptrs, y_ptrs,
+                                                                 g.ticket, g.tw);
+}
+
+cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, float2 *const *y_ptrs,
+                           cudaStream_t st) {
+    switch (g.log2N) {
+        case 8: batched_launch_n<8>(g, s_ptrs, y_ptrs, st); break;
+        case 9: batched_launch_n<9>(g, s_ptrs, y_ptrs, st); break;
+        case 10: batched_launch_n<10>(g, s_ptrs, y_ptrs, st); break;
+        case 11: batched_launch_n<11>(g, s_ptrs, y_ptrs, st); break;
+        case 12: batched_launch_n<12>(g, s_ptrs, y_ptrs, st); break;
+        case 13: batched_launch_n<13>(g, s_ptrs, y_ptrs, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ols

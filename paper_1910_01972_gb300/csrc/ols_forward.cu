@@ -32,8 +32,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
-#include "ols_fft_passes.cuh"
 #include "ols_internal.h"
+#include "ols_segment.cuh"
 
 namespace ols {
 
@@ -55,67 +55,11 @@ ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *_
     for (int i = threadIdx.x; i < G::TWN; i += G::BLOCK) tw[i] = twg[i];
     __syncthreads();
 #endif
-
-    const int lo = M - 1;                      // aliased samples per segment
     int xc = 0;
     const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
     for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
         const long long seg = blk * G::SEGS + slot;
-        const bool active = seg < nseg;
-        const long long start = seg * L;
-
-        // Segment load: samples start + k T + t, zero past Ns.
-        float2 X[16];
-        {
-            const long long avail = active ? (Ns - start) : 0;
-            const int lim = (int)(avail < G::N ? avail : G::N);
-            const float2 *src = sig + (active ? start : 0) + t;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
-        }
-        forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
-
-        // Valid outputs of this segment: n in [lo, lo + span), n = k T + t.
-        long long rem = active ? (Nout - start) : 0;
-        const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
-        const long long obase = start - lo;
-
-#if OLS_PREFETCH_H
-        float4 hn[8];
-#pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
-#endif
-        for (int f = 0; f < F; ++f) {
-            float2 x[16];
-#if OLS_PREFETCH_H
-#pragma unroll
-            for (int j2 = 0; j2 < 8; ++j2) {
-                x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].y));
-                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
-            }
-            if (f + 1 < F) {
-                const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
-#pragma unroll
-                for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
-            }
-#else
-            const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
-#pragma unroll
-            for (int j2 = 0; j2 < 8; ++j2) {
-                const float4 h = load_spectrum(hp + j2 * G::T);
-                x[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
-                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
-            }
-#endif
-            inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
-            float2 *dst = y + (size_t)f * (size_t)Nout;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int n = k * G::T + t;
-                if ((unsigned)(n - lo) < (unsigned)span) dst[obase + n] = x[k];
-            }
-        }
+        ols_segment<LOG2N>(sig, Ns, Hk, tw, y, M, F, L, Nout, seg, seg < nseg, bufs, t, xc);
     }
 }
 

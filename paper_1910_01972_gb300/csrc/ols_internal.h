@@ -31,6 +31,9 @@ PassPlan make_pass_plan(int log2N);
 // Frequency index held at each storage position of the forward FFT output.
 void spectral_order(int log2N, int32_t *nu);
 
+// Model-based segment length (no measurement): minimises (N / L)(log2 N + c).
+int64_t choose_segment_length(int32_t M);
+
 struct Staging {            // device buffers of ols_convolve_host
     float2 *in[2] = {nullptr, nullptr};
     float2 *out[2] = {nullptr, nullptr};
@@ -72,6 +75,30 @@ struct BackwardArgs {
     float2 *edge, *dh_part;   // workspace parts
     int grid, npart;
 };
+
+// One problem of a batch, as the batched kernel reads it.
+struct BatchProblemDev {
+    const float4 *Hk;     // spectra in kernel layout
+    long long Ns, Nout, L, nseg;
+    int M, F;
+    int index;            // position in the caller's pointer arrays
+    int pad;
+};
+
+// One persistent launch: every problem of the batch with segment length 2^log2N.
+struct BatchGroup {
+    int log2N = 0;
+    int grid = 0;
+    long long nitems = 0;
+    const BatchProblemDev *probs = nullptr;   // device
+    const int2 *items = nullptr;              // device: (problem in group, tile)
+    unsigned long long *ticket = nullptr;     // device counter, zeroed before each launch
+    const float2 *tw = nullptr;               // twiddles of this N (from one of the problems' plans)
+};
+
+cudaError_t batched_prepare(int log2N, int sm_count, int *grid_cap, int *segs);
+cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, float2 *const *y_ptrs,
+                           cudaStream_t st);
 
 // Forward fused OLS (Algorithm 2).  Returns a cudaError_t.
 cudaError_t launch_forward(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y,

@@ -1,0 +1,76 @@
+// ols_segment.cuh -- one segment of Algorithm 2, shared by the plain and the
+// batched fused kernels: load the segment (zero past Ns), forward FFT into
+// registers, then for every filter: point-wise product with its spectrum
+// (the next filter's spectrum already in flight), inverse FFT, and store of
+// the samples not aliased (n >= M-1) that fall inside the output.
+#pragma once
+
+#include "ols_fft_passes.cuh"
+
+namespace ols {
+
+template <int LOG2N>
+__device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long long Ns,
+                                            const float4 *__restrict__ Hk, const float2 *tw,
+                                            float2 *__restrict__ y, int M, int F, long long L,
+                                            long long Nout, long long seg, bool active, float2 *bufs,
+                                            int t, int &xc) {
+    using G = Geo<LOG2N>;
+    const int lo = M - 1;                      // aliased samples per segment
+    const long long start = seg * L;
+
+    // Segment load: samples start + k T + t, zero past Ns.
+    float2 X[16];
+    {
+        const long long avail = active ? (Ns - start) : 0;
+        const int lim = (int)(avail < G::N ? avail : G::N);
+        const float2 *src = sig + (active ? start : 0) + t;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+    }
+    forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
+
+    // Valid outputs of this segment: n in [lo, lo + span), n = k T + t.
+    const long long rem = active ? (Nout - start) : 0;
+    const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
+    const long long obase = start - lo;
+
+#if OLS_PREFETCH_H
+    float4 hn[8];
+#pragma unroll
+    for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
+#endif
+    for (int f = 0; f < F; ++f) {
+        float2 x[16];
+#if OLS_PREFETCH_H
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2) {
+            x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].y));
+            x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
+        }
+        if (f + 1 < F) {
+            const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+        }
+#else
+        const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2) {
+            const float4 h = load_spectrum(hp + j2 * G::T);
+            x[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
+            x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
+        }
+#endif
+        inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
+        float2 *dst = y + (size_t)f * (size_t)Nout;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int n = k * G::T + t;
+            if ((unsigned)(n - lo) < (unsigned)span) dst[obase + n] = x[k];
+        }
+    }
+}
+
+}  // namespace ols
