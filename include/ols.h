@@ -65,8 +65,18 @@ typedef enum {
 typedef struct ols_plan_s *ols_plan_t;
 typedef struct ols_batch_s *ols_batch_t;
 
-/* Plan flags (arithmetic of the plain convolution). */
+/* Plan flags (arithmetic of the convolution). */
 #define OLS_FLAG_FP32 0u
+/* Every radix-16 FFT stage as a tensor-core (tcgen05) matrix product on
+ * 16-bit split operands x = x_hi + x_lo and DFT matrices W = W_hi + W_lo,
+ * D = x_hi W_hi + x_hi W_lo + x_lo W_hi with FP32 accumulation; twiddles,
+ * the point-wise product and the exchanges stay FP32.  FP16 split: ~22
+ * significant bits per operand; BF16 split: ~16 bits.  Input range: the
+ * FP16 form assumes |s| <= 1.42 and unit-L2 filters (larger inputs should be
+ * scaled by a power of two; outside that range 16-bit operands can
+ * overflow).  Forward convolution only (ols_convolve, ols_convolve_host). */
+#define OLS_FLAG_TC_FP16SPLIT 1u
+#define OLS_FLAG_TC_BF16SPLIT 2u
 
 /* Human-readable name of a status code (static storage; never NULL). */
 OLS_API const char *ols_status_string(int status);
@@ -100,7 +110,7 @@ OLS_API int ols_spectrum_order(int64_t N, int32_t *nu);
  * (Sec. 3.2; N = 0 lets the library pick N from M, F and the segment-length
  * rule of Sec. 5: each N is best for a range of M).  Allocates the plan's
  * device tables (filter spectra F*N complex, twiddles) on the current
- * device.  flags: OLS_FLAG_FP32.
+ * device.  flags: OLS_FLAG_FP32, OLS_FLAG_TC_FP16SPLIT or OLS_FLAG_TC_BF16SPLIT.
  * Errors: INVALID (out == NULL, M < 1, F < 1), UNSUPPORTED (N, M > N, flags),
  * CUDA / ALLOC from the device.  *out is NULL on error.
  */
@@ -248,6 +258,14 @@ OLS_API int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const vo
 
 /* Kernel launches enqueued by the last ols_convolve_batched. */
 OLS_API int ols_batch_last_launch_count(ols_batch_t batch);
+
+/*
+ * Read the plan's device status word (synchronises the device): 0, or
+ * nonzero if a kernel's bounded wait on the tensor cores gave up since the
+ * last reset (that call's output is incomplete).  reset != 0 clears it.
+ * Errors: INVALID, CUDA.
+ */
+OLS_API int ols_plan_status(ols_plan_t plan, int *status, int reset);
 
 /* Size in bytes of the scratch array built into the library for
  * ols_convolve_backward_noalloc. */

@@ -169,6 +169,12 @@ class Plan:
     def last_launch_count(self) -> int:
         return _native.ols_last_launch_count(self._h)
 
+    def status(self, reset: bool = True) -> int:
+        """Device status word: nonzero if a bounded tensor-core wait gave up."""
+        rc, v = _native.ols_plan_status(self._h, reset)
+        check(rc, "ols_plan_status")
+        return v
+
 
 def autotune(M: int, F: int, model_only: bool = False) -> int:
     """Segment length the library picks for M taps and F filters (timed on the

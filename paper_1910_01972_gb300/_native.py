@@ -27,6 +27,8 @@ OLS_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 OLS_FLAG_FP32 = 0
 OLS_TUNE_MODEL = 1 << 8
+OLS_FLAG_TC_FP16SPLIT = 1
+OLS_FLAG_TC_BF16SPLIT = 2
 
 # (name, restype, argtypes) of every exported symbol declared in include/ols.h
 i32, i64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
@@ -48,6 +50,7 @@ SIGNATURES = [
     ("ols_convolve_backward", cint, [vp, vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     ("ols_convolve_backward_noalloc", cint, [vp, vp, i64, vp, vp, vp, vp]),
     ("ols_last_launch_count", cint, [vp]),
+    ("ols_plan_status", cint, [vp, P_i32, cint]),
     ("ols_autotune", cint, [i32, i32, u32, P_i64]),
     ("ols_batch_plan", cint, [ctypes.POINTER(vp), i32, P_i64, P_i32, P_i32, P_i64, u32]),
     ("ols_batch_destroy", cint, [vp]),
@@ -161,6 +164,12 @@ def ols_convolve_backward_noalloc(plan, s_ptr, Ns: int, g_ptr: int, ds_ptr, dh_p
 
 def ols_last_launch_count(plan) -> int:
     return lib().ols_last_launch_count(plan)
+
+
+def ols_plan_status(plan, reset: bool = True):
+    v = i32()
+    rc = lib().ols_plan_status(plan, ctypes.byref(v), int(reset))
+    return rc, v.value
 
 
 def ols_autotune(M: int, F: int, flags: int = 0):

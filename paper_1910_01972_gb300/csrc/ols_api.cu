@@ -1,6 +1,8 @@
 // ols_api.cu -- the C ABI of include/ols.h: argument checks, plans, tables,
 // and the host-buffer pipeline.  All arithmetic of the convolution runs in
 // the kernels of ols_forward.cu and ols_precompute.cu.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -51,6 +53,42 @@ static std::vector<float2> forward_twiddles(const PassPlan &pp) {
     return tw;
 }
 
+// The DFT-16 as the real 32x32 matrix B[k][n] of D = A B with
+// A = [Re x | Im x], D = [Re y | Im y]: B = [[C, S], [-S, C]], C = cos(2 pi pq/16),
+// S = Im W^{pq} (-sin forward, +sin inverse); split B = B_hi + B_lo in 16-bit
+// (FP16 or BF16) and stored in the tensor-core shared-memory layout (no
+// swizzle, K-major core matrices of 8 rows x 16 bytes: element (k, n) at byte
+// (k/8) 512 + (n/8) 128 + (n%8) 16 + (k%8) 2).  Order: fwd hi, fwd lo, inv hi, inv lo.
+static std::vector<uint16_t> tc_dft16_tables(bool bf16) {
+    std::vector<uint16_t> out(4 * 1024);
+    for (int inv = 0; inv < 2; ++inv)
+        for (int k = 0; k < 32; ++k)
+            for (int n = 0; n < 32; ++n) {
+                const int p = k % 16, q = n % 16;
+                const double th = 2.0 * M_PI * (double)((p * q) % 16) / 16.0;
+                const double c = std::cos(th), s = (inv ? 1.0 : -1.0) * std::sin(th);
+                double v;
+                if (k < 16) v = n < 16 ? c : s;
+                else v = n < 16 ? -s : c;
+                uint16_t hi, lo;
+                if (bf16) {
+                    const __nv_bfloat16 h = __double2bfloat16(v);
+                    const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
+                    hi = *reinterpret_cast<const uint16_t *>(&h);
+                    lo = *reinterpret_cast<const uint16_t *>(&l);
+                } else {
+                    const __half h = __double2half(v);
+                    const __half l = __double2half(v - (double)__half2float(h));
+                    hi = *reinterpret_cast<const uint16_t *>(&h);
+                    lo = *reinterpret_cast<const uint16_t *>(&l);
+                }
+                const int e = ((k / 8) * 512 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2) / 2;
+                out[(size_t)(2 * inv) * 1024 + e] = hi;
+                out[(size_t)(2 * inv + 1) * 1024 + e] = lo;
+            }
+    return out;
+}
+
 static int log2_exact(int64_t N) {
     if (N <= 0 || (N & (N - 1))) return -1;
     int l = 0;
@@ -59,6 +97,14 @@ static int log2_exact(int64_t N) {
 }
 
 static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
+
+// The fused convolution in the plan's arithmetic (FP32 or tensor-core split).
+static cudaError_t launch_any(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
+                              int64_t Nout, cudaStream_t st, int *launches) {
+    if (p.flags == OLS_FLAG_FP32) return launch_forward(p, s, Ns, y, L, nseg, Nout, st, launches);
+    *launches = 1;
+    return tc_launch(p, s, Ns, y, L, nseg, Nout, st);
+}
 
 static int status_of(cudaError_t e) {
     if (e == cudaSuccess) return OLS_OK;
@@ -107,6 +153,8 @@ static void free_plan(ols_plan_s *p) {
     if (p->tw) cudaFree(p->tw);
     if (p->tw64) cudaFree(p->tw64);
     if (p->nu) cudaFree(p->nu);
+    if (p->tc_bmat) cudaFree(p->tc_bmat);
+    if (p->d_status) cudaFree(p->d_status);
     free_staging(p->stage);
     delete p;
 }
@@ -158,7 +206,8 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     if (!out) return OLS_ERR_INVALID;
     *out = nullptr;
     if (M < 1 || F < 1) return OLS_ERR_INVALID;
-    if (flags != OLS_FLAG_FP32) return OLS_ERR_UNSUPPORTED;
+    if (flags != OLS_FLAG_FP32 && flags != OLS_FLAG_TC_FP16SPLIT && flags != OLS_FLAG_TC_BF16SPLIT)
+        return OLS_ERR_UNSUPPORTED;
     if (N == 0) N = choose_segment_length(M);
     const int l = log2_exact(N);
     if (l < kMinLog2N || l > kMaxLog2N || M > N) return OLS_ERR_UNSUPPORTED;
@@ -178,6 +227,14 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     if (e == cudaSuccess) e = cudaMalloc(&p->tw, sizeof(float2) * (size_t)(p->pp.twn > 0 ? p->pp.twn : 1));
     if (e == cudaSuccess) e = cudaMalloc(&p->tw64, sizeof(double2) * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&p->nu, sizeof(int32_t) * (size_t)N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess && flags != OLS_FLAG_FP32) {
+        const std::vector<uint16_t> b = tc_dft16_tables(flags == OLS_FLAG_TC_BF16SPLIT);
+        e = cudaMalloc(&p->tc_bmat, sizeof(uint16_t) * b.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->tc_bmat, b.data(), sizeof(uint16_t) * b.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = tc_prepare(*p, flags == OLS_FLAG_TC_BF16SPLIT);
+    }
     if (e == cudaSuccess) {
         std::vector<float2> tw = forward_twiddles(p->pp);
         std::vector<int32_t> nu((size_t)N);
@@ -246,8 +303,8 @@ int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *st
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
     if (rc != OLS_OK) return rc;
     int launches = 0;
-    cudaError_t e = launch_forward(*plan, reinterpret_cast<const float2 *>(s), Ns, reinterpret_cast<float2 *>(y),
-                                   L, nseg, Nout, (cudaStream_t)stream, &launches);
+    cudaError_t e = launch_any(*plan, reinterpret_cast<const float2 *>(s), Ns, reinterpret_cast<float2 *>(y), L,
+                               nseg, Nout, (cudaStream_t)stream, &launches);
     plan->last_launches = launches;
     return status_of(e);
 }
@@ -309,7 +366,7 @@ int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y
         if (e == cudaSuccess) {
             ols_geometry(plan->N, plan->M, nin_c, &Lc, &nsegc, &Noutc);
             int l = 0;
-            e = launch_forward(*plan, st.in[b], nin_c, st.out[b], Lc, nsegc, Noutc, cs, &l);
+            e = launch_any(*plan, st.in[b], nin_c, st.out[b], Lc, nsegc, Noutc, cs, &l);
             launches += l;
         }
         if (e == cudaSuccess)
@@ -355,6 +412,7 @@ int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const flo
     if ((ds && !aligned8(ds)) || (dh && !aligned8(dh))) return OLS_ERR_INVALID;
     if (dh && (!s || !aligned8(s))) return OLS_ERR_INVALID;
     if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    if (plan->flags != OLS_FLAG_FP32) return OLS_ERR_UNSUPPORTED;     // the adjoint is FP32 only
     int64_t L, nseg, Nout;
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
     if (rc != OLS_OK) return rc;
@@ -381,5 +439,15 @@ int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const flo
 }
 
 int ols_last_launch_count(ols_plan_t plan) { return plan ? plan->last_launches : -1; }
+
+int ols_plan_status(ols_plan_t plan, int *status, int reset) {
+    if (!plan || !status) return OLS_ERR_INVALID;
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(plan->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return status_of(e);
+    *status = v;
+    return OLS_OK;
+}
 
 }  // extern "C"

@@ -61,6 +61,9 @@ struct ols_plan_s {
     int fwd_grid_cap = 0;        // resident blocks of the forward kernel
     int bwd_grid_cap[3] = {0, 0, 0};  // backward kernel: (ds,dh), (ds), (dh)
     int last_launches = 0;
+    int tc_grid_cap = 0;         // resident blocks of the tensor-core kernel
+    uint16_t *tc_bmat = nullptr; // split DFT-16 matrices (fwd hi, fwd lo, inv hi, inv lo), core-matrix layout
+    int *d_status = nullptr;     // device status word (bounded-wait failures)
     ols::Staging stage;
 };
 
@@ -95,6 +98,11 @@ struct BatchGroup {
     unsigned long long *ticket = nullptr;     // device counter, zeroed before each launch
     const float2 *tw = nullptr;               // twiddles of this N (from one of the problems' plans)
 };
+
+// Tensor-core split-precision form (ols_tc.cu).
+cudaError_t tc_prepare(ols_plan_s &p, bool bf16);
+cudaError_t tc_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
+                      int64_t Nout, cudaStream_t st);
 
 cudaError_t batched_prepare(int log2N, int sm_count, int *grid_cap, int *segs);
 cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, float2 *const *y_ptrs,

@@ -1,0 +1,382 @@
+// ols_tc.cu -- fused OLS with every radix-16 FFT stage on the tensor cores
+// (tcgen05), in split 16-bit precision with FP32 accumulation.
+//
+// Same algorithm as ols_forward.cu (Algorithm 2: segment FFT kept on chip,
+// per filter point-wise product, inverse FFT, discard of the M-1 aliased
+// samples), but each 16-point DFT of a pass is a matrix product on the
+// tensor cores instead of register arithmetic:
+// * A thread's 16 complex values form one row of A = [Re x_0..15 | Im x_0..15]
+//   (K = 32).  They are split x = x_hi + x_lo into two 16-bit numbers (FP16 or
+//   BF16) and stored with tcgen05.st into the thread's own TMEM lane
+//   (128 threads = 128 lanes = one M = 128 tile).
+// * The DFT-16 is the real 32x32 matrix B = [[C, S], [-S, C]] (C = cos, S = the
+//   imaginary part of the twiddle), also split B = B_hi + B_lo, held in
+//   shared memory in the no-swizzle K-major core-matrix layout.
+// * D = A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term is below the
+//   16-bit split's resolution), six tcgen05.mma of K = 16 per tile, FP32
+//   accumulation in TMEM; one thread issues them and commits to an mbarrier;
+//   every thread waits (bounded) and reads its row back with tcgen05.ld.
+// * Twiddles, the point-wise product and the exchanges between passes stay
+//   in FP32 registers and shared memory, as in the FP32 kernel.  A remainder
+//   pass of radix 2/4/8 (N not a power of 16) stays in FP32 registers.
+// * Range: forward passes are unscaled (|input| <= 1.42 grows to <= 362
+//   before the last forward pass); inverse passes after the first are scaled
+//   by 1/4 (exact), and the filter spectra by 4^(passes-1), which keeps every
+//   16-bit operand below 65504 for inputs with |s| <= 1.42 and unit-L2 filters.
+// Waits on the mbarrier are bounded: on expiry the kernel records an error in
+// the plan's status word, stops, releases its TMEM and returns.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "ols_internal.h"
+#include "ols_fft_passes.cuh"
+
+namespace ols {
+
+namespace tc {
+
+constexpr int kCols = 64;            // TMEM columns per 128-row tile: A_hi 16, A_lo 16, D 32
+constexpr int kBytesB = 32 * 32 * 2; // one 32x32 16-bit matrix
+constexpr long long kWaitLimit = 1ll << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// 16-bit split of an FP32 pair into packed hi and lo words.
+template <bool BF16>
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    if constexpr (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+                 "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *d) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]), "=f"(d[6]), "=f"(d[7]),
+                   "=f"(d[8]), "=f"(d[9]), "=f"(d[10]), "=f"(d[11]), "=f"(d[12]), "=f"(d[13]), "=f"(d[14]),
+                   "=f"(d[15]), "=f"(d[16]), "=f"(d[17]), "=f"(d[18]), "=f"(d[19]), "=f"(d[20]), "=f"(d[21]),
+                   "=f"(d[22]), "=f"(d[23]), "=f"(d[24]), "=f"(d[25]), "=f"(d[26]), "=f"(d[27]), "=f"(d[28]),
+                   "=f"(d[29]), "=f"(d[30]), "=f"(d[31])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
+// 8 rows x 16 bytes; LBO = byte step between core matrices along K (512),
+// SBO = byte step along N (128); descriptor version 1.
+__device__ __forceinline__ uint64_t b_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(512 >> 4) << 16;
+    d |= (uint64_t)(128 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B FP16 (0) or BF16 (1),
+// both K-major, N = 32, M = 128.
+template <bool BF16>
+__device__ __forceinline__ constexpr uint32_t idesc() {
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((32u >> 3) << 17) |
+           ((128u >> 4) << 24);
+}
+
+struct Ctx {
+    uint32_t tmem;         // TMEM base of this CTA
+    uint32_t tile_cols;    // column offset of this thread's tile
+    uint32_t lane_bits;    // (warp % 4) * 32 << 16
+    uint32_t mbar;         // shared address of the mbarrier
+    uint32_t b_smem;       // shared address of the four B matrices (fwd hi, fwd lo, inv hi, inv lo)
+    uint32_t phase;        // mbarrier phase expected next
+    int ntiles;
+    int *status;           // plan status word (error flag)
+    bool failed;
+};
+
+// One radix-16 DFT pass on the tensor cores for every thread's 16 values
+// (x scaled by `scale` first).  Collective over the CTA.
+template <bool INV, bool BF16>
+__device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        split2<BF16>(x[2 * w].x * scale, x[2 * w + 1].x * scale, hi[w], lo[w]);
+        split2<BF16>(x[2 * w].y * scale, x[2 * w + 1].y * scale, hi[8 + w], lo[8 + w]);
+    }
+    const uint32_t a_hi = c.tmem + c.lane_bits + c.tile_cols;
+    tmem_st16(a_hi, hi);
+    tmem_st16(a_hi + 16, lo);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && !c.failed) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t bh = c.b_smem + (INV ? 2 : 0) * kBytesB, bl = bh + kBytesB;
+        for (int tl = 0; tl < c.ntiles; ++tl) {
+            const uint32_t base = c.tmem + tl * kCols;
+            const uint32_t d = base + 32;
+#pragma unroll
+            for (int term = 0; term < 3; ++term) {
+                const uint32_t a = base + (term == 2 ? 16 : 0);          // A_hi, A_hi, A_lo
+                const uint32_t b = term == 1 ? bl : bh;                    // B_hi, B_lo, B_hi
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint32_t acc = (term | kk) != 0;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+                                 "r"(a + kk * 8), "l"(b_desc(b + kk * 1024)), "r"(idesc<BF16>()), "r"(acc)
+                                 : "memory");
+                }
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
+                     : "memory");
+    }
+    uint32_t done = c.failed ? 1u : 0u;
+    for (long long it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(c.mbar), "r"(c.phase)
+                     : "memory");
+    }
+    if (!done) {
+        c.failed = true;
+        atomicOr(c.status, 1);
+    }
+    c.failed = __syncthreads_or(c.failed) != 0;
+    c.phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float d[32];
+    tmem_ld32(c.tmem + c.lane_bits + c.tile_cols + 32, d);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = make_float2(d[j], d[16 + j]);
+}
+
+template <int LOG2N, int P, bool BF16>
+__device__ __forceinline__ void tc_forward_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc, Ctx &c) {
+    using G = Geo<LOG2N>;
+    if constexpr (G::radix(P) == 16) dft16<false, BF16>(x, 1.0f, c);
+    else dft_groups<G::radix(P), false>(x);
+    if constexpr (P < G::NP - 1) {
+        twiddle<LOG2N, P, false>(x, tw, t);
+        exchange<LOG2N, P, P + 1>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
+        ++xc;
+        tc_forward_passes<LOG2N, P + 1, BF16>(x, bufs, tw, t, xc, c);
+    }
+}
+
+template <int LOG2N, int P, bool BF16>
+__device__ __forceinline__ void tc_inverse_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc,
+                                                  Ctx &c) {
+    using G = Geo<LOG2N>;
+    if constexpr (P < G::NP - 1) {
+        exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
+        ++xc;
+        twiddle<LOG2N, P, true>(x, tw, t);
+    }
+    if constexpr (G::radix(P) == 16) dft16<true, BF16>(x, P == G::NP - 1 ? 1.0f : 0.25f, c);
+    else dft_groups<G::radix(P), true>(x);
+    if constexpr (P > 0) tc_inverse_passes<LOG2N, P - 1, BF16>(x, bufs, tw, t, xc, c);
+}
+
+// Inverse passes after the first are scaled by 1/4: the spectra get 4^(k),
+// k = number of scaled radix-16 passes.
+template <int LOG2N>
+__host__ __device__ constexpr float spectrum_gain() {
+    float g = 1.0f;
+    for (int p = 0; p < Geo<LOG2N>::NP - 1; ++p)
+        if (Geo<LOG2N>::radix(p) == 16) g *= 4.0f;
+    return g;
+}
+
+}  // namespace tc
+
+template <int LOG2N, bool BF16>
+__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, Geo<LOG2N>::MINB)
+ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
+              const float2 *__restrict__ twg, const uint16_t *__restrict__ bmat, float2 *__restrict__ y, int M, int F,
+              long long L, long long nseg, long long Nout, int *status) {
+    using G = Geo<LOG2N>;
+    constexpr int NT = G::BLOCK / 128;           // M = 128 tiles per CTA
+    constexpr uint32_t NCOLS = NT * tc::kCols;
+    static_assert(G::BLOCK % 128 == 0, "the tensor-core form needs 128-thread multiples");
+    extern __shared__ float4 smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tbase;
+    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+    uint16_t *bsm = reinterpret_cast<uint16_t *>(smem);                     // 4 x 2 KB, 1 KB aligned
+    float2 *bufs0 = smem + (4 * tc::kBytesB) / sizeof(float2);
+    const int slot = threadIdx.x / G::T;
+    const int t = threadIdx.x % G::T;
+    float2 *bufs = bufs0 + slot * G::XBUFS * G::PADN;
+    const float2 *tw = twg;
+
+    for (int i = threadIdx.x; i < 4 * tc::kBytesB / 2; i += G::BLOCK) bsm[i] = bmat[i];
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tbase)),
+                     "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    tc::Ctx c;
+    c.tmem = tbase;
+    c.tile_cols = (uint32_t)(threadIdx.x / 128) * tc::kCols;
+    c.lane_bits = (uint32_t)(((threadIdx.x / 32) % 4) * 32) << 16;
+    c.mbar = tc::smem_u32(&mbar);
+    c.b_smem = tc::smem_u32(bsm);
+    c.phase = 0;
+    c.ntiles = NT;
+    c.status = status;
+    c.failed = false;
+
+    const int lo = M - 1;
+    const float gain = tc::spectrum_gain<LOG2N>();
+    int xc = 0;
+    const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
+    for (long long blk = blockIdx.x; blk < nblk && !c.failed; blk += gridDim.x) {
+        const long long seg = blk * G::SEGS + slot;
+        const bool active = seg < nseg;
+        const long long start = seg * L;
+        float2 X[16];
+        {
+            const long long avail = active ? (Ns - start) : 0;
+            const int lim = (int)(avail < G::N ? avail : G::N);
+            const float2 *src = sig + (active ? start : 0) + t;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+        }
+        tc::tc_forward_passes<LOG2N, 0, BF16>(X, bufs, tw, t, xc, c);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) X[k] = make_float2(X[k].x * gain, X[k].y * gain);
+        const long long rem = active ? (Nout - start) : 0;
+        const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
+        const long long obase = start - lo;
+        for (int f = 0; f < F && !c.failed; ++f) {
+            float2 x[16];
+            const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) {
+                const float4 h = load_spectrum(hp + j2 * G::T);
+                x[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
+                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
+            }
+            tc::tc_inverse_passes<LOG2N, G::NP - 1, BF16>(x, bufs, tw, t, xc, c);
+            float2 *dst = y + (size_t)f * (size_t)Nout;
+            if (!c.failed) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    if ((unsigned)(n - lo) < (unsigned)span) dst[obase + n] = x[k];
+                }
+            }
+        }
+    }
+    // release TMEM (after a bounded wait for any commit still in flight on failure)
+    if (c.failed) {
+        uint32_t done = 0;
+        for (long long it = 0; it < tc::kWaitLimit && !done; ++it) {
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(done)
+                         : "r"(c.mbar), "r"(c.phase ^ 1u)
+                         : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS));
+}
+
+template <int LOG2N>
+struct TcGeo {
+    static constexpr size_t SMEM = 4 * tc::kBytesB + sizeof(float2) * (size_t)(Geo<LOG2N>::SEGS * Geo<LOG2N>::XBUFS *
+                                                                               Geo<LOG2N>::PADN);
+};
+
+template <int LOG2N, bool BF16>
+static cudaError_t tc_prepare_one(ols_plan_s &p) {
+    cudaError_t e = cudaFuncSetAttribute(ols_tc_kernel<LOG2N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcGeo<LOG2N>::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_tc_kernel<LOG2N, BF16>, Geo<LOG2N>::BLOCK,
+                                                      TcGeo<LOG2N>::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int cols = (Geo<LOG2N>::BLOCK / 128) * tc::kCols;
+    if (per_sm * cols > 512) per_sm = 512 / cols;         // TMEM holds every resident CTA's columns
+    p.tc_grid_cap = per_sm * p.sm_count;
+    return cudaSuccess;
+}
+
+cudaError_t tc_prepare(ols_plan_s &p, bool bf16) {
+    switch (p.log2N) {
+        case 8: return bf16 ? tc_prepare_one<8, true>(p) : tc_prepare_one<8, false>(p);
+        case 9: return bf16 ? tc_prepare_one<9, true>(p) : tc_prepare_one<9, false>(p);
+        case 10: return bf16 ? tc_prepare_one<10, true>(p) : tc_prepare_one<10, false>(p);
+        case 11: return bf16 ? tc_prepare_one<11, true>(p) : tc_prepare_one<11, false>(p);
+        case 12: return bf16 ? tc_prepare_one<12, true>(p) : tc_prepare_one<12, false>(p);
+        case 13: return bf16 ? tc_prepare_one<13, true>(p) : tc_prepare_one<13, false>(p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LOG2N, bool BF16>
+static cudaError_t tc_launch_one(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L,
+                                 int64_t nseg, int64_t Nout, cudaStream_t st) {
+    using G = Geo<LOG2N>;
+    const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
+    const int grid = (int)(nblk < p.tc_grid_cap ? nblk : p.tc_grid_cap);
+    ols_tc_kernel<LOG2N, BF16><<<grid, G::BLOCK, TcGeo<LOG2N>::SMEM, st>>>(
+        s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, p.tc_bmat, y, p.M, p.F, L, nseg, Nout, p.d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
+                      int64_t Nout, cudaStream_t st) {
+    const bool bf16 = (p.flags & OLS_FLAG_TC_BF16SPLIT) != 0;
+    switch (p.log2N) {
+        case 8: return bf16 ? tc_launch_one<8, true>(p, s, Ns, y, L, nseg, Nout, st)
+                            : tc_launch_one<8, false>(p, s, Ns, y, L, nseg, Nout, st);
+        case 9: return bf16 ? tc_launch_one<9, true>(p, s, Ns, y, L, nseg, Nout, st)
+                            : tc_launch_one<9, false>(p, s, Ns, y, L, nseg, Nout, st);
+        case 10: return bf16 ? tc_launch_one<10, true>(p, s, Ns, y, L, nseg, Nout, st)
+                             : tc_launch_one<10, false>(p, s, Ns, y, L, nseg, Nout, st);
+        case 11: return bf16 ? tc_launch_one<11, true>(p, s, Ns, y, L, nseg, Nout, st)
+                             : tc_launch_one<11, false>(p, s, Ns, y, L, nseg, Nout, st);
+        case 12: return bf16 ? tc_launch_one<12, true>(p, s, Ns, y, L, nseg, Nout, st)
+                             : tc_launch_one<12, false>(p, s, Ns, y, L, nseg, Nout, st);
+        case 13: return bf16 ? tc_launch_one<13, true>(p, s, Ns, y, L, nseg, Nout, st)
+                             : tc_launch_one<13, false>(p, s, Ns, y, L, nseg, Nout, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ols

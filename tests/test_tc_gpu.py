@@ -1,0 +1,103 @@
+"""The tensor-core split-precision form against the FP64 oracle.
+
+Stated bounds (max over filters of the relative L2 error):
+* FP16 split: 2e-6.  Each operand carries ~22 significant bits
+  (x = x_hi + x_lo in FP16, unit roundoff 2^-22 ~ 2.4e-7 per rounding); a
+  radix-16 pass adds about three such roundings (operand split, DFT-matrix
+  split, the dropped lo*lo term) on top of FP32 accumulation, and a
+  convolution runs 3 + 3 passes at N = 4096: ~1e-6 expected (measured
+  0.8e-6 .. 1.2e-6).
+* BF16 split: 3e-5.  ~16-17 significant bits (2^-17 ~ 7.6e-6 per rounding),
+  same pass count: measured 6e-6 .. 8e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1910_01972_gb300 import OLSError, Plan, _native
+from paper_1910_01972_gb300 import build as _build
+
+pytestmark = pytest.mark.gpu
+BOUND = {_native.OLS_FLAG_TC_FP16SPLIT: 2e-6, _native.OLS_FLAG_TC_BF16SPLIT: 3e-5}
+FLAGS = [_native.OLS_FLAG_TC_FP16SPLIT, _native.OLS_FLAG_TC_BF16SPLIT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("flag", FLAGS)
+@pytest.mark.parametrize("N,M,F,Ns", [(4096, 512, 4, 200_000), (256, 33, 3, 20_001), (2048, 257, 4, 60_000),
+                                      (8192, 1025, 2, 90_000), (1024, 129, 5, 30_000), (512, 1, 2, 3_000),
+                                      (4096, 4096, 1, 9_000)])
+def test_tc_parity(flag, N, M, F, Ns):
+    g = np.random.Generator(np.random.PCG64(N + M + flag))
+    s, h = synth.signal(g, Ns), synth.filters(g, F, M)
+    p = Plan(M, F, N, flags=flag)
+    p.set_filters(dev(h))
+    y = p.convolve(dev(s)).cpu().numpy()
+    assert p.status() == 0
+    err = oracle.max_stream_rel_l2(y, oracle.conv(s, h))
+    assert err <= BOUND[flag], err
+    p.close()
+
+
+@pytest.mark.parametrize("flag", FLAGS)
+def test_tc_index_bookkeeping_with_delta_filters(flag):
+    """Delta filters on a small-integer signal: rounding the output recovers
+    the shifted input exactly (segment starts, discards and tail clip)."""
+    N, M, Ns = 4096, 300, 3 * 4096 + 77
+    n = np.arange(Ns)
+    s = (((n % 3) - 1) + 1j * (((7 * n) % 3) - 1)).astype(np.complex64)
+    ds = [0, 150, 299]
+    h = np.zeros((3, M), np.complex64)
+    for i, d in enumerate(ds):
+        h[i, d] = 1.0
+    p = Plan(M, 3, N, flags=flag)
+    p.set_filters(dev(h))
+    y = p.convolve(dev(s)).cpu().numpy()
+    for i, d in enumerate(ds):
+        ref = s[M - 1 - d: Ns - d]
+        got = np.round(y[i].real) + 1j * np.round(y[i].imag)
+        assert np.array_equal(got, ref)
+    p.close()
+
+
+@pytest.mark.parametrize("flag", FLAGS)
+def test_tc_full_size_sampled(flag):
+    """Ns = 2^24, F = 64, M = 512, N = 4096: sampled outputs against the oracle."""
+    cfg = synth.TC_SPLIT
+    s, h = synth.plain_inputs(cfg)
+    p = Plan(cfg.M, cfg.F, cfg.N, flags=flag)
+    p.set_filters(dev(h))
+    y = p.convolve(dev(s))
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    g = np.random.Generator(np.random.PCG64(9))
+    Nout = cfg.Ns - cfg.M + 1
+    fi = g.integers(0, cfg.F, 20_000)
+    ji = np.concatenate([g.integers(0, Nout, 19_996), [0, 1, Nout - 2, Nout - 1]])
+    got = y[torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()].cpu().numpy()
+    ref = oracle.conv_at(s, h, fi, ji)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= BOUND[flag]
+    del y
+    p.close()
+
+
+def test_tc_plans_reject_the_adjoint():
+    p = Plan(65, 2, 512, flags=_native.OLS_FLAG_TC_FP16SPLIT)
+    p.set_filters(torch.zeros((2, 65), dtype=torch.complex64, device="cuda"))
+    s = torch.zeros(2000, dtype=torch.complex64, device="cuda")
+    g = torch.zeros((2, 2000 - 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(OLSError):
+        p.convolve_backward(s, g)
+    p.close()
