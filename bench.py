@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ns", type=int, default=0, help="override the signal length (profiling a smaller case)")
+    ap.add_argument("--no-others", action="store_true", help="skip the other workloads (batched, adjoint, tensor-core)")
     return ap.parse_args()
 
 
@@ -199,6 +200,183 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ other workloads
+def _time_events(fn, reps, flush=None):
+    """Mean device time (ms) of fn() over reps calls, each bracketed by events
+    on the current stream; an optional L2 flush runs between calls, outside
+    the events."""
+    import torch
+    st = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def measure_others(peak):
+    """Throughput of the other workloads on this GPU (outputs and samples for
+    oracle checks are returned separately; the oracle runs in the CPU leg)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import BatchPlan, Plan, _native
+    res, samples = {}, {}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")       # 256 MB > L2
+
+    # one signal, one filter (65,536 samples, M = 64, N = 512): fits in L2, so flush between calls
+    cfg = synth.PLAIN_1x1
+    s_np, h_np = synth.plain_inputs(cfg)
+    p = Plan(cfg.M, cfg.F, cfg.N)
+    p.set_filters(torch.from_numpy(h_np).cuda())
+    s = torch.from_numpy(s_np).cuda()
+    y = p.convolve(s)
+    ms = _time_events(lambda: p.convolve(s, out=y), 50, flush)
+    nout = cfg.Ns - cfg.M + 1
+    res["plain_1x1"] = {"workload": cfg.name, "value": nout / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                        "note": "L2 flushed between calls; launch-latency bound (146 segments)"}
+    p.close()
+
+    # differentiable shape: forward + adjoint (ds and dh)
+    cfg = synth.DIFF
+    s_np, h_np, w_np = synth.diff_inputs(cfg)
+    p = Plan(cfg.M, cfg.F, cfg.N)
+    p.set_filters(torch.from_numpy(h_np).cuda())
+    s = torch.from_numpy(s_np).cuda()
+    y = p.convolve(s)
+    gy = (2.0 * torch.from_numpy(w_np).cuda()[None, :] * y).contiguous()
+    nout = cfg.Ns - cfg.M + 1
+    ms_f = _time_events(lambda: p.convolve(s, out=y), 10)
+    nb = p.backward_workspace(cfg.Ns)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    wp = (ws.data_ptr() + 255) & ~255
+    ds = torch.empty(cfg.Ns, dtype=torch.complex64, device="cuda")
+    dh = torch.empty((cfg.F, cfg.M), dtype=torch.complex64, device="cuda")
+    stp = torch.cuda.current_stream().cuda_stream
+
+    def bwd():
+        _native.check(_native.ols_convolve_backward(p.handle, s.data_ptr(), cfg.Ns, gy.data_ptr(), ds.data_ptr(),
+                                                    dh.data_ptr(), wp, nb, stp), "ols_convolve_backward")
+    bwd()
+    ms_b = _time_events(bwd, 10)
+    b_bytes = 8 * cfg.Ns + 8 * cfg.F * nout + 8 * cfg.Ns + 8 * cfg.F * cfg.M
+    res["diff"] = {"workload": cfg.name, "forward": {"value": cfg.F * nout / (ms_f * 1e-3), "unit": UNIT, "ms": ms_f},
+                   "backward": {"value": cfg.F * nout / (ms_b * 1e-3), "unit": "gradient samples/s (F*(Ns-M+1))",
+                                "ms": ms_b, "hbm_frac": b_bytes / (ms_b * 1e-3) / 1e9 / peak,
+                                "algorithmic_bytes": b_bytes}}
+    samples["diff"] = None
+    p.close()
+    del y, gy, ds, dh, ws
+
+    # uneven batch: one graph replay of the batched launches vs 64 per-signal plain launches
+    spec = synth.batch_spec()
+    ss, hs = synth.batch_inputs(spec)
+    bp = BatchPlan(spec.Ns, spec.M, spec.F)
+    bp.set_filters([torch.from_numpy(h).cuda() for h in hs])
+    sd = [torch.from_numpy(x).cuda() for x in ss]
+    ys = bp.outputs()
+    st_t, yt_t = bp.pointer_table(sd), bp.pointer_table(ys)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        bp.launch(st_t, yt_t)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            bp.launch(st_t, yt_t)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    outs = sum(f * n for f, n in zip(spec.F, bp.Nout))
+    ms_g = _time_events(graph.replay, 5)
+    plans = []
+    for b in range(bp.B):
+        q = Plan(spec.M[b], spec.F[b], bp.N[b])
+        q.set_filters(torch.from_numpy(hs[b]).cuda())
+        plans.append(q)
+
+    def per_signal():
+        for b in range(bp.B):
+            plans[b].convolve(sd[b], out=ys[b])
+    per_signal()
+    ms_p = _time_events(per_signal, 5)
+    in_bytes = 8 * sum(spec.Ns)
+    bb = in_bytes + 8 * outs
+    res["batched"] = {"workload": "batch_B64_Ns2^16..2^22_F8..128_M33..1025_autotuned",
+                      "value": outs / (ms_g * 1e-3), "unit": UNIT, "ms": ms_g, "hbm_frac": bb / (ms_g * 1e-3) / 1e9 / peak,
+                      "launches": bp.ngroups, "segment_lengths": sorted(set(bp.N)),
+                      "per_signal": {"value": outs / (ms_p * 1e-3), "ms": ms_p, "launches": bp.B},
+                      "speedup_vs_per_signal": ms_p / ms_g, "total_outputs": outs}
+    graph.replay()
+    torch.cuda.synchronize()
+    g = np.random.Generator(np.random.PCG64(5))
+    picks = []
+    for b in range(0, bp.B, 8):
+        fi = g.integers(0, spec.F[b], 32)
+        ji = g.integers(0, bp.Nout[b], 32)
+        got = ys[b][torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()].cpu().numpy()
+        picks.append((ss[b], hs[b], fi, ji, got))
+    samples["batched"] = picks
+    for q in plans:
+        q.close()
+    bp.close()
+    del ys, sd, graph
+
+    # tensor-core split precision vs FP32 on the same inputs
+    cfg = synth.TC_SPLIT
+    s_np, h_np = synth.plain_inputs(cfg)
+    s = torch.from_numpy(s_np).cuda()
+    h = torch.from_numpy(h_np).cuda()
+    nout = cfg.Ns - cfg.M + 1
+    y = torch.empty((cfg.F, nout), dtype=torch.complex64, device="cuda")
+    tcres = {}
+    g = np.random.Generator(np.random.PCG64(6))
+    fi = g.integers(0, cfg.F, 4000)
+    ji = g.integers(0, nout, 4000)
+    samples["tc"] = {"s": s_np, "h": h_np, "fi": fi, "ji": ji}
+    for flag, name in ((0, "fp32"), (_native.OLS_FLAG_TC_FP16SPLIT, "fp16split"), (_native.OLS_FLAG_TC_BF16SPLIT,
+                                                                                     "bf16split")):
+        q = Plan(cfg.M, cfg.F, cfg.N, flags=flag)
+        q.set_filters(h)
+        q.convolve(s, out=y)
+        ms = _time_events(lambda: q.convolve(s, out=y), 5)
+        tb = 8 * cfg.Ns + 8 * cfg.F * nout
+        tcres[name] = {"value": cfg.F * nout / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                       "hbm_frac": tb / (ms * 1e-3) / 1e9 / peak, "status": q.status()}
+        torch.cuda.synchronize()
+        samples["tc"][name] = y[torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()].cpu().numpy()
+        q.close()
+    res["tensor_core"] = {"workload": cfg.name, **tcres}
+    del y, s, h
+    torch.cuda.empty_cache()
+    return res, samples
+
+
+def others_errors(samples):
+    """Relative L2 errors of the other workloads' sampled outputs against the oracle."""
+    import numpy as np
+    import oracle
+    out = {}
+    if samples.get("batched"):
+        num = den = 0.0
+        for s, h, fi, ji, got in samples["batched"]:
+            ref = oracle.conv_at(s, h, fi, ji)
+            num += float(np.sum(np.abs(got - ref) ** 2))
+            den += float(np.sum(np.abs(ref) ** 2))
+        out["batched"] = (num / den) ** 0.5
+    if samples.get("tc"):
+        d = samples["tc"]
+        ref = oracle.conv_at(d["s"], d["h"], d["fi"], d["ji"])
+        for name in ("fp32", "fp16split", "bf16split"):
+            out["tc_" + name] = float(np.linalg.norm(d[name] - ref) / np.linalg.norm(ref))
+    return out
+
+
 # ------------------------------------------------------------------ our leg
 def run_ours(args):
     import numpy as np
@@ -307,6 +485,9 @@ def run_ours(args):
                "steps": args.e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * cfg.F * Nout,
                "path": "ols_convolve_host: pinned host buffers, chunked H2D / kernel / D2H on two streams"}
         del y_host, s_host
+    others, samples = (None, None)
+    if rank == 0 and world == 1 and not args.no_others and not args.ns:
+        others, samples = measure_others(peak)
     clk = clocks.stop()
 
     cpu = None
@@ -316,6 +497,8 @@ def run_ours(args):
         err = max(float(np.linalg.norm(got[f] - y_ref[f]) / np.linalg.norm(y_ref[f])) for f in range(cfg.F))
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
                "gpu_rel_l2_on_sample": err}
+        if samples:
+            cpu["other_workloads_rel_l2_on_samples"] = others_errors(samples)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -333,6 +516,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
+        "others": others,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
