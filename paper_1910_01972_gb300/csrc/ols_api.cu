@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -35,6 +36,21 @@ void spectral_order(int log2N, int32_t *nu) {
         }
         nu[q0] = v;
     }
+}
+
+void spectral_order_w64(int32_t *nu) {
+    for (int q = 0; q < 2048; ++q) nu[q] = (q >> 6) + 32 * (q & 63);
+}
+
+// W_2048^(n' k) for k in [1, 32), n' in [0, 64), index (k-1) 64 + n'.
+static std::vector<float2> w64_twiddles() {
+    std::vector<float2> tw(31 * 64);
+    for (int k = 1; k < 32; ++k)
+        for (int n = 0; n < 64; ++n) {
+            const double a = -2.0 * M_PI * (double)((n * k) % 2048) / 2048.0;
+            tw[(size_t)(k - 1) * 64 + n] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    return tw;
 }
 
 static std::vector<float2> forward_twiddles(const PassPlan &pp) {
@@ -99,8 +115,21 @@ static int log2_exact(int64_t N) {
 static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
 
 // The fused convolution in the plan's arithmetic (FP32 or tensor-core split).
+// The N = 2048 single-warp-per-segment kernel (64 points per thread, one
+// exchange per FFT) is opt-in with OLS_W64_KERNEL=1: on GB300 it measures
+// slower than the 16-points-per-thread kernel (two warps per scheduler cannot
+// hide its latencies).
+static bool use_w64() {
+    const char *v = std::getenv("OLS_W64_KERNEL");
+    return v && v[0] == '1';
+}
+
 static cudaError_t launch_any(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
                               int64_t Nout, cudaStream_t st, int *launches) {
+    if (p.flags == OLS_FLAG_FP32 && p.Hk_w64) {
+        *launches = 1;
+        return w64_launch(p, s, Ns, y, L, nseg, Nout, st);
+    }
     if (p.flags == OLS_FLAG_FP32) return launch_forward(p, s, Ns, y, L, nseg, Nout, st, launches);
     *launches = 1;
     return tc_launch(p, s, Ns, y, L, nseg, Nout, st);
@@ -154,6 +183,9 @@ static void free_plan(ols_plan_s *p) {
     if (p->tw64) cudaFree(p->tw64);
     if (p->nu) cudaFree(p->nu);
     if (p->tc_bmat) cudaFree(p->tc_bmat);
+    if (p->Hk_w64) cudaFree(p->Hk_w64);
+    if (p->tw_w64) cudaFree(p->tw_w64);
+    if (p->nu_w64) cudaFree(p->nu_w64);
     if (p->d_status) cudaFree(p->d_status);
     free_staging(p->stage);
     delete p;
@@ -229,6 +261,17 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     if (e == cudaSuccess) e = cudaMalloc(&p->nu, sizeof(int32_t) * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess && flags == OLS_FLAG_FP32 && l == 11 && use_w64()) {
+        std::vector<float2> tw = w64_twiddles();
+        std::vector<int32_t> nu(2048);
+        spectral_order_w64(nu.data());
+        e = cudaMalloc(&p->Hk_w64, sizeof(float2) * (size_t)F * (size_t)N);
+        if (e == cudaSuccess) e = cudaMalloc(&p->tw_w64, sizeof(float2) * tw.size());
+        if (e == cudaSuccess) e = cudaMalloc(&p->nu_w64, sizeof(int32_t) * nu.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->tw_w64, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->nu_w64, nu.data(), sizeof(int32_t) * nu.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = w64_prepare(*p);
+    }
     if (e == cudaSuccess && flags != OLS_FLAG_FP32) {
         const std::vector<uint16_t> b = tc_dft16_tables(flags == OLS_FLAG_TC_BF16SPLIT);
         e = cudaMalloc(&p->tc_bmat, sizeof(uint16_t) * b.size());
@@ -279,10 +322,13 @@ int ols_plan_query(ols_plan_t plan, int64_t Ns, int64_t *N, int32_t *M, int32_t 
 int ols_set_filters(ols_plan_t plan, const float *h, void *stream) {
     if (!plan || !h || !aligned8(h)) return OLS_ERR_INVALID;
     const float2 *hh = reinterpret_cast<const float2 *>(h);
-    cudaError_t e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0,
+    cudaError_t e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0, 0,
                                    (cudaStream_t)stream);
     if (e == cudaSuccess)
-        e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Htk, 1,
+        e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Htk, 1, 0,
+                           (cudaStream_t)stream);
+    if (e == cudaSuccess && plan->Hk_w64)
+        e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu_w64, plan->tw64, plan->Hk_w64, 0, 1,
                            (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
     plan->filters_ready = true;

@@ -25,15 +25,22 @@ ols_batched_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__rest
     using G = Geo<LOG2N>;
     extern __shared__ float4 smem_raw[];
     __shared__ long long item_sh;
+    __shared__ uint32_t tbase;
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
-    float2 *bufs = smem + G::TWN_PAD + slot * G::XBUFS * G::PADN;
-#if OLS_TW_GLOBAL
-    const float2 *tw = twg;
+    float2 *bufs = smem + slot * G::XBUFS * G::PADN;
+#if OLS_FWD_TW_TMEM
+    // twiddles in TMEM: warp 0 allocates, every thread fills its own lane
+    if (threadIdx.x < 32) tmem::alloc(&tbase, G::TMEM_COLS);
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N>(twg, tw.base, t);
 #else
-    float2 *tw = smem;
-    for (int i = threadIdx.x; i < G::TWN; i += G::BLOCK) tw[i] = twg[i];
+    (void)tbase;
+    const TwGlobal tw{twg};
 #endif
     int xc = 0;
     for (;;) {
@@ -49,18 +56,25 @@ ols_batched_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__rest
         ols_segment<LOG2N>(s_ptrs[P.index], P.Ns, P.Hk, tw, y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
                            seg < nseg, bufs, t, xc);
     }
+#if OLS_FWD_TW_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, G::TMEM_COLS);
+#endif
 }
 
 template <int LOG2N>
 static cudaError_t batched_prepare_n(int sm_count, int *grid_cap, int *segs) {
     using G = Geo<LOG2N>;
     cudaError_t e = cudaFuncSetAttribute(ols_batched_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::SMEM);
+                                         (int)G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_kernel<LOG2N>, G::BLOCK, G::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (OLS_FWD_TW_TMEM && per_sm > G::TMEM_MAX_CTAS) per_sm = G::TMEM_MAX_CTAS;
     *grid_cap = per_sm * sm_count;
     *segs = G::SEGS;
     return cudaSuccess;
@@ -82,7 +96,7 @@ template <int LOG2N>
 static void batched_launch_n(const BatchGroup &g, const float2 *const *s_ptrs, float2 *const *y_ptrs,
                              cudaStream_t st) {
     using G = Geo<LOG2N>;
-    ols_batched_kernel<LOG2N><<<g.grid, G::BLOCK, G::SMEM, st>>>(g.probs, g.items, g.nitems, s_ptrs, y_ptrs,
+    ols_batched_kernel<LOG2N><<<g.grid, G::BLOCK, G::SMEM_TMEM, st>>>(g.probs, g.items, g.nitems, s_ptrs, y_ptrs,
                                                                  g.ticket, g.tw);
 }
 

@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "fft_regs.cuh"
+#include "tmem.cuh"
 
 // Tuning knobs (compile-time; defaults are the measured best on GB300).
 #ifndef OLS_PREFETCH_H
@@ -34,6 +35,9 @@
 #endif
 #ifndef OLS_TW_GLOBAL
 #define OLS_TW_GLOBAL 1      // twiddles read through L1 (1) or staged in shared memory (0)
+#endif
+#ifndef OLS_FWD_TW_TMEM
+#define OLS_FWD_TW_TMEM 0    // 1: fused kernels keep twiddles and the segment spectrum in TMEM
 #endif
 #ifndef OLS_WARPS_PER_SM
 #define OLS_WARPS_PER_SM 16  // resident warps per SM the register budget must allow
@@ -62,6 +66,15 @@ struct Geo {
     static constexpr int TWN_PAD = OLS_TW_GLOBAL ? 0 : ((TWN + 1) & ~1);   // keep buffers 16-byte aligned
     static constexpr int XBUFS = OLS_XBUFS;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * XBUFS * PADN);
+    // TMEM twiddles: 128 columns per 128 threads (a thread's lane, 32 columns per pass)
+    static constexpr uint32_t TMEM_COLS = (uint32_t)(BLOCK / 128) * 128u;
+    static constexpr int TMEM_MAX_CTAS = 512 / (int)TMEM_COLS;
+    // shared memory requested with TMEM twiddles: enough that no more CTAs fit on
+    // an SM (228 KB) than TMEM can serve, so allocation never waits
+    static constexpr size_t SMEM_TMEM = !OLS_FWD_TW_TMEM ? SMEM
+                                        : (SEGS * XBUFS * PADN * sizeof(float2) > (228u * 1024u) / (TMEM_MAX_CTAS + 1))
+                                            ? SEGS * XBUFS * PADN * sizeof(float2)
+                                            : (228u * 1024u) / (TMEM_MAX_CTAS + 1) + 1024u;
 };
 
 // Padded shared-memory base of thread t in the layout of pass P:
@@ -91,48 +104,154 @@ __device__ __forceinline__ void exchange(float2 *x, float2 *buf, int t) {
     for (int k = 0; k < 16; ++k) x[k] = buf[br + pad_off<LOG2N, PR>(k)];
 }
 
-// Multiply element k of pass P's 16-point group by W_{16 s}^{(t mod s) k}
-// (conjugated for the inverse).
-template <int LOG2N, int P, bool INV>
-__device__ __forceinline__ void twiddle(float2 *x, const float2 *tw, int t) {
-    using G = Geo<LOG2N>;
-    constexpr int s = G::stride(P);
-    const float2 *w = tw + G::tw_off(P) + (t % s);
-#pragma unroll
-    for (int k = 1; k < 16; ++k) {
-#if OLS_TW_GLOBAL
-        const float2 wk = __ldg(w + (k - 1) * s);
-#else
-        const float2 wk = w[(k - 1) * s];
+// Twiddle sources.  Element k of pass P's 16-point group is multiplied by
+// W_{16 s}^{(t mod s) k} (s = the pass's stride), conjugated for the inverse.
+// Each source splits the step into fetch() (issue the loads) and apply()
+// (wait and multiply), so the pass functions can put a barrier-bound
+// exchange between the two and hide the load latency.
+//
+// TwGlobal: read through L1 from the plan's table (entry (k-1) s + n' of
+// pass P at offset tw_off(P)).
+// Only the first OLS_TW_LOADS powers w^1.. of a pass's twiddle are loaded
+// (1, 2, 4 or 15); the others are formed as products (w^2 = w w, w^3 = w w^2,
+// w^4 = w^2 w^2, w^8 = w^4 w^4, w^12 = w^4 w^8, w^k = w^(k&3) w^(k&12)), at
+// most five roundings deep for a single load: the L1 data path, the binding
+// resource of the fused kernel, is traded for FP32 multiplies, which have
+// headroom.
+#ifndef OLS_TW_LOADS
+#define OLS_TW_LOADS 4
 #endif
-        x[k] = ctw<INV>(x[k], wk);
+#define OLS_TW_RECUR (OLS_TW_LOADS < 15)
+struct TwGlobal {
+    const float2 *tw;
+    struct Fetched {
+        float2 w[OLS_TW_LOADS];
+    };
+    template <int LOG2N, int P>
+    __device__ __forceinline__ void fetch(Fetched &f, int t) const {
+        using G = Geo<LOG2N>;
+        constexpr int s = G::stride(P);
+        const float2 *w = tw + G::tw_off(P) + (t % s);
+#pragma unroll
+        for (int k = 1; k <= OLS_TW_LOADS; ++k) {
+#if OLS_TW_GLOBAL
+            f.w[k - 1] = __ldg(w + (k - 1) * s);
+#else
+            f.w[k - 1] = w[(k - 1) * s];
+#endif
+        }
+    }
+    template <bool INV>
+    __device__ __forceinline__ void apply(float2 *x, const Fetched &f) const {
+#if OLS_TW_RECUR
+        float2 w[16];
+#pragma unroll
+        for (int k = 1; k <= OLS_TW_LOADS; ++k) w[k] = f.w[k - 1];
+        if (OLS_TW_LOADS < 2) w[2] = cmul(w[1], w[1]);
+        if (OLS_TW_LOADS < 3) w[3] = cmul(w[1], w[2]);
+        if (OLS_TW_LOADS < 4) w[4] = cmul(w[2], w[2]);
+        w[8] = cmul(w[4], w[4]);
+        w[12] = cmul(w[4], w[8]);
+#pragma unroll
+        for (int k = 5; k < 16; ++k)
+            if (k != 8 && k != 12) w[k] = cmul(w[k & 3], w[k & 12]);
+#pragma unroll
+        for (int k = 1; k < 16; ++k) x[k] = ctw<INV>(x[k], w[k]);
+#else
+#pragma unroll
+        for (int k = 1; k < 16; ++k) x[k] = ctw<INV>(x[k], f.w[k - 1]);
+#endif
+    }
+};
+
+// TwTmem: the thread's own 15 twiddles of every pass, preloaded into its
+// TMEM lane (pass P at columns 32 P .. 32 P + 29 of `base`): no L1 traffic.
+struct TwTmem {
+    uint32_t base;
+    struct Fetched {
+        float v[32];
+    };
+    template <int LOG2N, int P>
+    __device__ __forceinline__ void fetch(Fetched &f, int) const {
+        tmem::ld32(base + 32 * P, f.v);
+    }
+    template <bool INV>
+    __device__ __forceinline__ void apply(float2 *x, const Fetched &f) const {
+        tmem::wait_ld();
+#pragma unroll
+        for (int k = 1; k < 16; ++k) x[k] = ctw<INV>(x[k], make_float2(f.v[2 * k - 2], f.v[2 * k - 1]));
+    }
+};
+
+// Fill a TwTmem for thread t from the plan's twiddle table.
+template <int LOG2N, int P = 0>
+__device__ __forceinline__ void tw_tmem_fill(const float2 *tw, uint32_t base, int t) {
+    using G = Geo<LOG2N>;
+    if constexpr (P < G::NP - 1) {
+        constexpr int s = G::stride(P);
+        const float2 *w = tw + G::tw_off(P) + (t % s);
+        float v[32];
+#pragma unroll
+        for (int k = 1; k < 16; ++k) {
+            const float2 wk = __ldg(w + (k - 1) * s);
+            v[2 * k - 2] = wk.x;
+            v[2 * k - 1] = wk.y;
+        }
+        v[30] = v[31] = 0.f;
+        tmem::st32(base + 32 * P, v);
+        tw_tmem_fill<LOG2N, P + 1>(tw, base, t);
+    } else {
+        tmem::wait_st();
     }
 }
 
-template <int LOG2N, int P>
-__device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {
+// One global-table twiddle step (fetch and apply back to back).
+template <int LOG2N, int P, bool INV>
+__device__ __forceinline__ void twiddle(float2 *x, const float2 *tw, int t) {
+    const TwGlobal g{tw};
+    TwGlobal::Fetched f;
+    g.template fetch<LOG2N, P>(f, t);
+    g.template apply<INV>(x, f);
+}
+
+template <int LOG2N, int P, class TW>
+__device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const TW &tw, int t, int &xc) {
     using G = Geo<LOG2N>;
-    dft_groups<G::radix(P), false>(x);
     if constexpr (P < G::NP - 1) {
-        twiddle<LOG2N, P, false>(x, tw, t);
+        typename TW::Fetched f;
+        tw.template fetch<LOG2N, P>(f, t);            // in flight during the DFT
+        dft_groups<G::radix(P), false>(x);
+        tw.template apply<false>(x, f);
         exchange<LOG2N, P, P + 1>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
         ++xc;
         forward_passes<LOG2N, P + 1>(x, bufs, tw, t, xc);
+    } else {
+        dft_groups<G::radix(P), false>(x);
     }
+}
+template <int LOG2N, int P>
+__device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {
+    forward_passes<LOG2N, P>(x, bufs, TwGlobal{tw}, t, xc);
 }
 
 // x holds pass P+1's layout (or pass NP-1's when P == NP-1); runs the
 // inverse of passes P, P-1, ..., 0.
-template <int LOG2N, int P>
-__device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {
+template <int LOG2N, int P, class TW>
+__device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const TW &tw, int t, int &xc) {
     using G = Geo<LOG2N>;
     if constexpr (P < G::NP - 1) {
+        typename TW::Fetched f;
+        tw.template fetch<LOG2N, P>(f, t);            // in flight during the exchange
         exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
         ++xc;
-        twiddle<LOG2N, P, true>(x, tw, t);
+        tw.template apply<true>(x, f);
     }
     dft_groups<G::radix(P), true>(x);
     if constexpr (P > 0) inverse_passes<LOG2N, P - 1>(x, bufs, tw, t, xc);
+}
+template <int LOG2N, int P>
+__device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {
+    inverse_passes<LOG2N, P>(x, bufs, TwGlobal{tw}, t, xc);
 }
 
 __device__ __forceinline__ float4 load_spectrum(const float4 *p) {

@@ -44,16 +44,22 @@ ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *_
                    long long L, long long nseg, long long Nout) {
     using G = Geo<LOG2N>;
     extern __shared__ float4 smem_raw[];
+    __shared__ uint32_t tbase;
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
-    float2 *bufs = smem + G::TWN_PAD + slot * G::XBUFS * G::PADN;
-#if OLS_TW_GLOBAL
-    const float2 *tw = twg;
-#else
-    float2 *tw = smem;
-    for (int i = threadIdx.x; i < G::TWN; i += G::BLOCK) tw[i] = twg[i];
+    float2 *bufs = smem + slot * G::XBUFS * G::PADN;
+#if OLS_FWD_TW_TMEM
+    // twiddles in TMEM: warp 0 allocates, every thread fills its own lane
+    if (threadIdx.x < 32) tmem::alloc(&tbase, G::TMEM_COLS);
+    tmem::fence_before_sync();
     __syncthreads();
+    tmem::fence_after_sync();
+    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N>(twg, tw.base, t);
+#else
+    (void)tbase;
+    const TwGlobal tw{twg};
 #endif
     int xc = 0;
     const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
@@ -61,18 +67,25 @@ ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *_
         const long long seg = blk * G::SEGS + slot;
         ols_segment<LOG2N>(sig, Ns, Hk, tw, y, M, F, L, Nout, seg, seg < nseg, bufs, t, xc);
     }
+#if OLS_FWD_TW_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, G::TMEM_COLS);
+#endif
 }
 
 template <int LOG2N>
 static cudaError_t prepare_one(ols_plan_s &p) {
     using G = Geo<LOG2N>;
     cudaError_t e = cudaFuncSetAttribute(ols_forward_kernel<LOG2N>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_forward_kernel<LOG2N>, G::BLOCK, G::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_forward_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (OLS_FWD_TW_TMEM && per_sm > G::TMEM_MAX_CTAS) per_sm = G::TMEM_MAX_CTAS;
     p.fwd_grid_cap = per_sm * p.sm_count;
     return cudaSuccess;
 }
@@ -83,7 +96,7 @@ static cudaError_t launch_one(const ols_plan_s &p, const float2 *s, int64_t Ns, 
     using G = Geo<LOG2N>;
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
     const int grid = (int)(nblk < p.fwd_grid_cap ? nblk : p.fwd_grid_cap);
-    ols_forward_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM, st>>>(
+    ols_forward_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM_TMEM, st>>>(
         s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y, p.M, p.F, L, nseg, Nout);
     return cudaGetLastError();
 }

@@ -62,6 +62,11 @@ struct ols_plan_s {
     int bwd_grid_cap[3] = {0, 0, 0};  // backward kernel: (ds,dh), (ds), (dh)
     int last_launches = 0;
     int tc_grid_cap = 0;         // resident blocks of the tensor-core kernel
+    // N = 2048 single-warp-per-segment kernel (passes 32 x 64)
+    float2 *Hk_w64 = nullptr;    // [F][N] spectra in its register layout
+    float2 *tw_w64 = nullptr;    // W_2048^(n' k), k in [1, 32), n' in [0, 64): index (k-1) 64 + n'
+    int32_t *nu_w64 = nullptr;   // its spectral order
+    int w64_grid_cap = 0;
     uint16_t *tc_bmat = nullptr; // split DFT-16 matrices (fwd hi, fwd lo, inv hi, inv lo), core-matrix layout
     int *d_status = nullptr;     // device status word (bounded-wait failures)
     ols::Staging stage;
@@ -99,6 +104,13 @@ struct BatchGroup {
     const float2 *tw = nullptr;               // twiddles of this N (from one of the problems' plans)
 };
 
+// N = 2048 single-warp-per-segment fused kernel (ols_w64.cu).
+cudaError_t w64_prepare(ols_plan_s &p);
+cudaError_t w64_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
+                       int64_t Nout, cudaStream_t st);
+// Spectral order of the 32 x 64 decomposition: position q = 64 t + j holds t + 32 j.
+void spectral_order_w64(int32_t *nu);
+
 // Tensor-core split-precision form (ols_tc.cu).
 cudaError_t tc_prepare(ols_plan_s &p, bool bf16);
 cudaError_t tc_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
@@ -121,8 +133,9 @@ int backward_grid(const ols_plan_s &p, int64_t nseg, bool want_ds, bool want_dh)
 int backward_segs_per_block(int log2N);
 // FP64 precompute kernels.  adjoint != 0 transforms conj(h_f[M-1-k]) instead of h_f[k].
 cudaError_t launch_tw64(double2 *tw64, int N, cudaStream_t st);
+// layout 0: the 16-points-per-thread kernels; layout 1: the N = 2048 64-points-per-thread kernel.
 cudaError_t launch_spectra(const float2 *h, int M, int F, int log2N, const int32_t *nu,
-                           const double2 *tw64, float2 *Hk, int adjoint, cudaStream_t st);
+                           const double2 *tw64, float2 *Hk, int adjoint, int layout, cudaStream_t st);
 cudaError_t launch_spectra_natural(const float2 *Hk, int F, int log2N, const int32_t *nu,
                                    float2 *H, cudaStream_t st);
 

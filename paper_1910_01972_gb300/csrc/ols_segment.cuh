@@ -1,17 +1,21 @@
 // ols_segment.cuh -- one segment of Algorithm 2, shared by the plain and the
 // batched fused kernels: load the segment (zero past Ns), forward FFT into
-// registers, then for every filter: point-wise product with its spectrum
-// (the next filter's spectrum already in flight), inverse FFT, and store of
-// the samples not aliased (n >= M-1) that fall inside the output.
+// registers (kept there for all filters; with TMEM twiddles, in the thread's
+// TMEM lane instead, columns 96..127), then for every filter: point-wise
+// product with its spectrum (the next filter's spectrum already in flight),
+// inverse FFT, and store of the samples not aliased (n >= M-1) that fall
+// inside the output.
 #pragma once
+
+#include <type_traits>
 
 #include "ols_fft_passes.cuh"
 
 namespace ols {
 
-template <int LOG2N>
+template <int LOG2N, class TW>
 __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long long Ns,
-                                            const float4 *__restrict__ Hk, const float2 *tw,
+                                            const float4 *__restrict__ Hk, const TW &tw,
                                             float2 *__restrict__ y, int M, int F, long long L,
                                             long long Nout, long long seg, bool active, float2 *bufs,
                                             int t, int &xc) {
@@ -30,6 +34,13 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
             X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
     }
     forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
+    constexpr bool x_in_tmem = std::is_same<TW, TwTmem>::value;
+    uint32_t xcol = 0;
+    if constexpr (x_in_tmem) {
+        xcol = tw.base + 96;
+        tmem::st32(xcol, reinterpret_cast<const float *>(X));
+        tmem::wait_st();
+    }
 
     // Valid outputs of this segment: n in [lo, lo + span), n = k T + t.
     const long long rem = active ? (Nout - start) : 0;
@@ -44,10 +55,17 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
     for (int f = 0; f < F; ++f) {
         float2 x[16];
 #if OLS_PREFETCH_H
+        if constexpr (x_in_tmem) {
+            tmem::ld32(xcol, reinterpret_cast<float *>(x));
+            tmem::wait_ld();
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = X[j];
+        }
 #pragma unroll
         for (int j2 = 0; j2 < 8; ++j2) {
-            x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].y));
-            x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
+            x[2 * j2] = cmul(x[2 * j2], make_float2(hn[j2].x, hn[j2].y));
+            x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
         }
         if (f + 1 < F) {
             const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
@@ -56,11 +74,18 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
         }
 #else
         const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
+        if constexpr (x_in_tmem) {
+            tmem::ld32(xcol, reinterpret_cast<float *>(x));
+            tmem::wait_ld();
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = X[j];
+        }
 #pragma unroll
         for (int j2 = 0; j2 < 8; ++j2) {
             const float4 h = load_spectrum(hp + j2 * G::T);
-            x[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
-            x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
+            x[2 * j2] = cmul(x[2 * j2], make_float2(h.x, h.y));
+            x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(h.z, h.w));
         }
 #endif
         inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
