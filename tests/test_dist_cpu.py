@@ -1,0 +1,85 @@
+"""Multi-rank splitting of one signal (paper_1910_01972_gb300.parallel) on CPU:
+world size 2 over gloo, each rank's shard computed by the FP64 oracle."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+from paper_1910_01972_gb300 import parallel
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+@pytest.mark.parametrize("Ns,M,world", [(1000, 33, 2), (1000, 33, 3), (70, 70, 2), (9, 1, 4), (100, 40, 7)])
+def test_shards_tile_the_outputs_and_inputs(Ns, M, world):
+    Nout = Ns - M + 1
+    seen_out = np.zeros(Nout, int)
+    seen_in = np.zeros(Ns, int)
+    for r in range(world):
+        j0, j1, i0, i1 = parallel.shard(Ns, M, world, r)
+        assert i0 == j0 and i1 == j1 + M - 1 and 0 <= i0 <= i1 <= Ns
+        seen_out[j0:j1] += 1
+        a, b = parallel.input_range(Ns, M, world, r)
+        seen_in[a:b] += 1
+    assert np.all(seen_out == 1) and np.all(seen_in == 1)
+
+
+def _worker(rank, world, port, Ns, M, F, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    import oracle
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g = np.random.Generator(np.random.PCG64(42))
+        s = (g.uniform(-1, 1, Ns) + 1j * g.uniform(-1, 1, Ns)).astype(np.complex64)
+        h = (g.normal(size=(F, M)) + 1j * g.normal(size=(F, M))).astype(np.complex64)
+        gy = g.normal(size=(F, Ns - M + 1)) + 1j * g.normal(size=(F, Ns - M + 1))
+        j0, j1, i0, i1 = parallel.shard(Ns, M, world, rank)
+        # forward: each rank convolves its slice, no communication
+        y_loc = torch.from_numpy(oracle.conv(s[i0:i1], h))
+        parts = [None] * world
+        dist.all_gather_object(parts, (j0, y_loc.numpy()))
+        # adjoint on the slice, then the two reductions
+        ds_loc, dh_loc = oracle.adjoint(s[i0:i1], h, gy[:, j0:j1])
+        ds_mine = parallel.reduce_input_gradient(torch.from_numpy(ds_loc), M, world, rank)
+        dh_all = parallel.reduce_filter_gradient(torch.from_numpy(dh_loc))
+        ds_parts = [None] * world
+        dist.all_gather_object(ds_parts, (parallel.input_range(Ns, M, world, rank), ds_mine.numpy()))
+        if rank == 0:
+            y = np.concatenate([p[1] for p in sorted(parts, key=lambda p: p[0])], axis=1)
+            y_ref = oracle.conv(s, h)
+            ds = np.zeros(Ns, np.complex128)
+            for (a, b), v in ds_parts:
+                ds[a:b] = v
+            ds_ref, dh_ref = oracle.adjoint(s, h, gy)
+            q.put((bool(np.array_equal(y, y_ref)),
+                   float(np.max(np.abs(ds - ds_ref)) / np.max(np.abs(ds_ref))),
+                   float(np.max(np.abs(dh_all.numpy() - dh_ref)) / np.max(np.abs(dh_ref)))))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2])
+def test_two_rank_split_equals_whole_signal(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    Ns, M, F = 3000, 65, 3
+    procs = [ctx.Process(target=_worker, args=(r, world, port, Ns, M, F, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    for p in procs:
+        assert p.exitcode == 0, "rank failed"
+    same_y, e_ds, e_dh = q.get(timeout=5)
+    assert same_y                      # each output is the same sequential sum: identical
+    assert e_ds < 1e-12 and e_dh < 1e-12
