@@ -41,6 +41,37 @@ __device__ __forceinline__ float2 sub_rot(float2 a, float2 b) {
     return INV ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
 }
 
+// Two complex numbers of two different segments in split form:
+// re = (Re a, Re b), im = (Im a, Im b).  Every complex operation on a pair is
+// the same per-lane arithmetic as on one float2, so results are bitwise those
+// of the single-segment code, with one packed instruction per two values.
+struct cpair {
+    float2 re, im;
+};
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ cpair cadd(cpair a, cpair b) { return {__fadd2_rn(a.re, b.re), __fadd2_rn(a.im, b.im)}; }
+__device__ __forceinline__ cpair csub(cpair a, cpair b) {
+    return {__fadd2_rn(a.re, neg2(b.re)), __fadd2_rn(a.im, neg2(b.im))};
+}
+template <bool INV>
+__device__ __forceinline__ cpair add_rot(cpair a, cpair b) {
+    return INV ? cpair{__fadd2_rn(a.re, neg2(b.im)), __fadd2_rn(a.im, b.re)}
+               : cpair{__fadd2_rn(a.re, b.im), __fadd2_rn(a.im, neg2(b.re))};
+}
+template <bool INV>
+__device__ __forceinline__ cpair sub_rot(cpair a, cpair b) {
+    return INV ? cpair{__fadd2_rn(a.re, b.im), __fadd2_rn(a.im, neg2(b.re))}
+               : cpair{__fadd2_rn(a.re, neg2(b.im)), __fadd2_rn(a.im, b.re)};
+}
+// a * (wr + i wi) with the factor given as broadcast pairs (wr, wr), (wi, wi)
+__device__ __forceinline__ cpair cmul(cpair a, float2 wr, float2 wi) {
+    return {__ffma2_rn(a.re, wr, neg2(__fmul2_rn(a.im, wi))), __ffma2_rn(a.re, wi, __fmul2_rn(a.im, wr))};
+}
+// a * conj(wr + i wi)
+__device__ __forceinline__ cpair cmulc(cpair a, float2 wr, float2 wi) {
+    return {__ffma2_rn(a.re, wr, __fmul2_rn(a.im, wi)), __ffma2_rn(a.im, wr, neg2(__fmul2_rn(a.re, wi)))};
+}
+
 // a * b
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -58,6 +89,19 @@ template <bool INV>
 __device__ __forceinline__ float2 rot_quarter(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
+template <bool INV>
+__device__ __forceinline__ cpair rot_quarter(cpair a) {
+    return INV ? cpair{neg2(a.im), a.re} : cpair{a.im, neg2(a.re)};
+}
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ cpair cneg(cpair a) { return {neg2(a.re), neg2(a.im)}; }
+// a * (wr + i wi) for compile-time constants
+__device__ __forceinline__ float2 cmul_const(float2 a, float wr, float wi) {
+    return make_float2(fmaf(a.x, wr, -a.y * wi), fmaf(a.x, wi, a.y * wr));
+}
+__device__ __forceinline__ cpair cmul_const(cpair a, float wr, float wi) {
+    return cmul(a, make_float2(wr, wr), make_float2(wi, wi));
+}
 
 // cos / sin of 2 pi e / 16 for e in [0, 16), as exact-as-float constants.
 __device__ __forceinline__ constexpr float c16(int e) {
@@ -71,13 +115,13 @@ __device__ __forceinline__ constexpr float s16(int e) { return c16((e + 12) & 15
 
 // a * exp(-+ 2 pi i E / 16): trivial rotations cost nothing, the rest a
 // complex multiply by a compile-time constant.
-template <int E, bool INV>
-__device__ __forceinline__ float2 rot16(float2 a) {
+template <int E, bool INV, class C>
+__device__ __forceinline__ C rot16(C a) {
     constexpr int e = E & 15;
     if constexpr (e == 0) {
         return a;
     } else if constexpr (e == 8) {
-        return make_float2(-a.x, -a.y);
+        return cneg(a);
     } else if constexpr (e == 4) {
         return rot_quarter<INV>(a);
     } else if constexpr (e == 12) {
@@ -85,21 +129,21 @@ __device__ __forceinline__ float2 rot16(float2 a) {
     } else {
         constexpr float wr = c16(e);
         constexpr float wi = INV ? s16(e) : -s16(e);
-        return make_float2(fmaf(a.x, wr, -a.y * wi), fmaf(a.x, wi, a.y * wr));
+        return cmul_const(a, wr, wi);
     }
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
-    const float2 t = a0;
+template <bool INV, class C>
+__device__ __forceinline__ void dft2(C &a0, C &a1) {
+    const C t = a0;
     a0 = cadd(t, a1);
     a1 = csub(t, a1);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-    const float2 u0 = cadd(a0, a2), u1 = csub(a0, a2);
-    const float2 v0 = cadd(a1, a3), d = csub(a1, a3);
+template <bool INV, class C>
+__device__ __forceinline__ void dft4(C &a0, C &a1, C &a2, C &a3) {
+    const C u0 = cadd(a0, a2), u1 = csub(a0, a2);
+    const C v0 = cadd(a1, a3), d = csub(a1, a3);
     a0 = cadd(u0, v0);
     a2 = csub(u0, v0);
     a1 = add_rot<INV>(u1, d);     // u1 + r (a1 - a3)
@@ -108,10 +152,10 @@ __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 
 
 // dft4 of (a0, a1, r a2, a3), r = -i (forward) / +i (inverse): the rotation of
 // a2 is folded into the first adds.
-template <bool INV>
-__device__ __forceinline__ void dft4_r2(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-    const float2 u0 = add_rot<INV>(a0, a2), u1 = sub_rot<INV>(a0, a2);
-    const float2 v0 = cadd(a1, a3), d = csub(a1, a3);
+template <bool INV, class C>
+__device__ __forceinline__ void dft4_r2(C &a0, C &a1, C &a2, C &a3) {
+    const C u0 = add_rot<INV>(a0, a2), u1 = sub_rot<INV>(a0, a2);
+    const C v0 = cadd(a1, a3), d = csub(a1, a3);
     a0 = cadd(u0, v0);
     a2 = csub(u0, v0);
     a1 = add_rot<INV>(u1, d);
@@ -120,13 +164,13 @@ __device__ __forceinline__ void dft4_r2(float2 &a0, float2 &a1, float2 &a2, floa
 
 // 8-point DFT in place on x[0..7] (natural order in and out): 8 = 4 x 2.
 // n = 2 n1 + n2, k = k1 + 4 k2:  DFT-4 over n1, rotate by W8^(n2 k1), DFT-2 over n2.
-template <bool INV>
-__device__ __forceinline__ void dft8(float2 *x) {
+template <bool INV, class C>
+__device__ __forceinline__ void dft8(C *x) {
     dft4<INV>(x[0], x[2], x[4], x[6]);   // n2 = 0 -> A[k1][0] at x[2 k1]
     dft4<INV>(x[1], x[3], x[5], x[7]);   // n2 = 1 -> A[k1][1] at x[2 k1 + 1]
     x[3] = rot16<2, INV>(x[3]);          // W8^1
     x[7] = rot16<6, INV>(x[7]);          // W8^3  (W8^2 = r on x[5] is folded below)
-    float2 y[8];
+    C y[8];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
         if (k1 == 2) {
@@ -143,8 +187,8 @@ __device__ __forceinline__ void dft8(float2 *x) {
 
 // 16-point DFT in place on x[0..15] (natural order in and out): 16 = 4 x 4.
 // n = 4 n1 + n2, k = k1 + 4 k2:  DFT-4 over n1, rotate by W16^(n2 k1), DFT-4 over n2.
-template <bool INV>
-__device__ __forceinline__ void dft16(float2 *x) {
+template <bool INV, class C>
+__device__ __forceinline__ void dft16(C *x) {
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
     // x[4 k1 + n2] = A[k1][n2]
@@ -161,7 +205,7 @@ __device__ __forceinline__ void dft16(float2 *x) {
     dft4_r2<INV>(x[8], x[9], x[10], x[11]);    // x[10] carries W16^4 = r
     dft4<INV>(x[12], x[13], x[14], x[15]);
     // x[4 k1 + k2] = X[k1 + 4 k2]; return natural order
-    float2 y[16];
+    C y[16];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1)
 #pragma unroll
@@ -194,15 +238,15 @@ __device__ __forceinline__ constexpr float c64(int e) {
 __device__ __forceinline__ constexpr float s64(int e) { return c64((e + 48) & 63); }  // sin = cos(x - pi/2)
 
 // a * exp(-+ 2 pi i E / 64).
-template <int E, bool INV>
-__device__ __forceinline__ float2 rot64(float2 a) {
+template <int E, bool INV, class C>
+__device__ __forceinline__ C rot64(C a) {
     constexpr int e = E & 63;
     if constexpr ((e & 3) == 0) {
         return rot16<e / 4, INV>(a);
     } else {
         constexpr float wr = c64(e);
         constexpr float wi = INV ? s64(e) : -s64(e);
-        return make_float2(fmaf(a.x, wr, -a.y * wi), fmaf(a.x, wi, a.y * wr));
+        return cmul_const(a, wr, wi);
     }
 }
 
@@ -268,8 +312,8 @@ __device__ __forceinline__ void dft64(float2 *x) {
 }
 
 // R-point DFT on each of the 16/R consecutive groups of x[0..15].
-template <int R, bool INV>
-__device__ __forceinline__ void dft_groups(float2 *x) {
+template <int R, bool INV, class C>
+__device__ __forceinline__ void dft_groups(C *x) {
     if constexpr (R == 16) {
         dft16<INV>(x);
     } else {

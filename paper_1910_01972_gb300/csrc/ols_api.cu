@@ -124,8 +124,21 @@ static bool use_w64() {
     return v && v[0] == '1';
 }
 
+// The two-segments-per-thread kernel (N = 2048 or 4096; bitwise the same
+// results) is opt-in with OLS_PAIR_KERNEL=1: it executes 28% fewer
+// instructions, but at 246 registers only 8 warps fit per SM and it measures
+// slower on GB300 than the 16-warp single-segment kernel.
+static bool use_pair() {
+    const char *v = std::getenv("OLS_PAIR_KERNEL");
+    return v && v[0] == '1';
+}
+
 static cudaError_t launch_any(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
                               int64_t Nout, cudaStream_t st, int *launches) {
+    if (p.flags == OLS_FLAG_FP32 && p.tw_pair) {
+        *launches = 1;
+        return pair_launch(p, s, Ns, y, L, nseg, Nout, st);
+    }
     if (p.flags == OLS_FLAG_FP32 && p.Hk_w64) {
         *launches = 1;
         return w64_launch(p, s, Ns, y, L, nseg, Nout, st);
@@ -184,6 +197,7 @@ static void free_plan(ols_plan_s *p) {
     if (p->nu) cudaFree(p->nu);
     if (p->tc_bmat) cudaFree(p->tc_bmat);
     if (p->Hk_w64) cudaFree(p->Hk_w64);
+    if (p->tw_pair) cudaFree(p->tw_pair);
     if (p->tw_w64) cudaFree(p->tw_w64);
     if (p->nu_w64) cudaFree(p->nu_w64);
     if (p->d_status) cudaFree(p->d_status);
@@ -261,6 +275,15 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     if (e == cudaSuccess) e = cudaMalloc(&p->nu, sizeof(int32_t) * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess && flags == OLS_FLAG_FP32 && (l == 11 || l == 12) && use_pair()) {
+        std::vector<float2> tw = forward_twiddles(p->pp);
+        std::vector<float4> tp(tw.size());
+        for (size_t i = 0; i < tw.size(); ++i) tp[i] = make_float4(tw[i].x, tw[i].x, tw[i].y, tw[i].y);
+        e = cudaMalloc(&p->tw_pair, sizeof(float4) * (tp.empty() ? 1 : tp.size()));
+        if (e == cudaSuccess && !tp.empty())
+            e = cudaMemcpy(p->tw_pair, tp.data(), sizeof(float4) * tp.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = pair_prepare(*p);
+    }
     if (e == cudaSuccess && flags == OLS_FLAG_FP32 && l == 11 && use_w64()) {
         std::vector<float2> tw = w64_twiddles();
         std::vector<int32_t> nu(2048);

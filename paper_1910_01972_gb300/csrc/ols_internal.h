@@ -67,6 +67,9 @@ struct ols_plan_s {
     float2 *tw_w64 = nullptr;    // W_2048^(n' k), k in [1, 32), n' in [0, 64): index (k-1) 64 + n'
     int32_t *nu_w64 = nullptr;   // its spectral order
     int w64_grid_cap = 0;
+    // two-segments-per-thread kernel (N >= 2048)
+    float4 *tw_pair = nullptr;   // twiddle table as broadcast pairs (wr, wr, wi, wi)
+    int pair_grid_cap = 0;
     uint16_t *tc_bmat = nullptr; // split DFT-16 matrices (fwd hi, fwd lo, inv hi, inv lo), core-matrix layout
     int *d_status = nullptr;     // device status word (bounded-wait failures)
     ols::Staging stage;
@@ -110,6 +113,11 @@ cudaError_t w64_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 
                        int64_t Nout, cudaStream_t st);
 // Spectral order of the 32 x 64 decomposition: position q = 64 t + j holds t + 32 j.
 void spectral_order_w64(int32_t *nu);
+
+// Two-segments-per-thread fused kernel, split form (ols_pair.cu), N >= 2048.
+cudaError_t pair_prepare(ols_plan_s &p);
+cudaError_t pair_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
+                        int64_t Nout, cudaStream_t st);
 
 // Tensor-core split-precision form (ols_tc.cu).
 cudaError_t tc_prepare(ols_plan_s &p, bool bf16);
