@@ -186,9 +186,11 @@ OLS_API int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int
  *   dh_f[k] = sum_j g_f[j] conj(s[j+M-1-k])                  device [F][M] complex, or NULL
  * (at least one of them non-NULL; s may be NULL when dh is NULL).  Computed
  * window by window in the frequency domain with the segment spectrum of s
- * recomputed, 2F+2 on-chip FFTs per window, then a small finishing kernel
- * (overlaps of ds, fixed-order compensated sum of the dh partials):
- * deterministic for a given plan and device.  Outputs are overwritten, not
+ * recomputed: F+2 on-chip FFTs per window (the signal segment, the F
+ * gradient windows, one inverse for ds); dh is summed over windows as a
+ * spectrum per CTA, then two small kernels add the ds overlaps, sum the
+ * CTAs' spectra in a fixed order (compensated) and run one inverse FFT per
+ * filter: deterministic for a given plan and device.  Outputs are overwritten, not
  * accumulated.  workspace: device buffer of at least ols_backward_workspace()
  * bytes, 256-byte aligned, owned by the caller; its contents on entry do not
  * matter.  Errors: INVALID (pointers), NOT_READY, UNSUPPORTED (ds wanted with

@@ -450,17 +450,18 @@ int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y
     return status_of(e);
 }
 
-// Workspace of the adjoint: overlap edges of ds (nseg x 2 x (M-1)), then the
-// per-slot dh partials (slots x F x M), each part 256-byte aligned.
+// Workspace of the adjoint: overlap edges of ds (nseg x 2 x (M-1) complex),
+// then the per-CTA dh spectra (grid x F x N complex) and their sum (F x N
+// complex), each part 256-byte aligned.
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static void backward_layout(const ols_plan_s &p, int64_t nseg, bool want_ds, bool want_dh, size_t *edge_bytes,
-                            size_t *part_bytes, int *grid, int *npart) {
+                            size_t *part_bytes, size_t *sum_bytes, int *grid) {
     *grid = backward_grid(p, nseg, want_ds, want_dh);
-    const int64_t slots = (int64_t)(*grid) * backward_segs_per_block(p.log2N);
-    *npart = (int)(slots < nseg ? slots : nseg);
     *edge_bytes = want_ds ? align256(sizeof(float2) * (size_t)nseg * 2 * (size_t)(p.M - 1)) : 0;
-    *part_bytes = want_dh ? align256(sizeof(float2) * (size_t)slots * (size_t)p.F * (size_t)p.M) : 0;
+    const size_t spec = sizeof(float2) * (size_t)p.F * (size_t)p.N;
+    *part_bytes = want_dh ? align256(spec * (size_t)(*grid)) : 0;
+    *sum_bytes = want_dh ? align256(spec) : 0;
 }
 
 int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int want_dh, size_t *bytes) {
@@ -468,10 +469,10 @@ int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int want_dh
     int64_t L, nseg, Nout;
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
     if (rc != OLS_OK) return rc;
-    size_t eb, pb;
-    int grid, npart;
-    backward_layout(*plan, nseg, want_ds != 0, want_dh != 0, &eb, &pb, &grid, &npart);
-    *bytes = eb + pb;
+    size_t eb, pb, rb;
+    int grid;
+    backward_layout(*plan, nseg, want_ds != 0, want_dh != 0, &eb, &pb, &rb, &grid);
+    *bytes = eb + pb + rb;
     return OLS_OK;
 }
 
@@ -486,10 +487,10 @@ int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const flo
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
     if (rc != OLS_OK) return rc;
     if (ds && plan->M - 1 > L) return OLS_ERR_UNSUPPORTED;   // ds overlaps must span two windows at most
-    size_t eb, pb;
+    size_t eb, pb, rb;
     BackwardArgs a{};
-    backward_layout(*plan, nseg, ds != nullptr, dh != nullptr, &eb, &pb, &a.grid, &a.npart);
-    if (eb + pb > 0 && (!workspace || workspace_bytes < eb + pb || ((uintptr_t)workspace & 255u)))
+    backward_layout(*plan, nseg, ds != nullptr, dh != nullptr, &eb, &pb, &rb, &a.grid);
+    if (eb + pb + rb > 0 && (!workspace || workspace_bytes < eb + pb + rb || ((uintptr_t)workspace & 255u)))
         return OLS_ERR_WORKSPACE;
     a.s = reinterpret_cast<const float2 *>(s);
     a.Ns = Ns;
@@ -500,7 +501,8 @@ int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const flo
     a.ds = reinterpret_cast<float2 *>(ds);
     a.dh = reinterpret_cast<float2 *>(dh);
     a.edge = eb ? reinterpret_cast<float2 *>(workspace) : nullptr;
-    a.dh_part = pb ? reinterpret_cast<float2 *>(static_cast<char *>(workspace) + eb) : nullptr;
+    a.P = pb ? reinterpret_cast<float4 *>(static_cast<char *>(workspace) + eb) : nullptr;
+    a.Pr = rb ? reinterpret_cast<float4 *>(static_cast<char *>(workspace) + eb + pb) : nullptr;
     int launches = 0;
     cudaError_t e = launch_backward(*plan, a, (cudaStream_t)stream, &launches);
     plan->last_launches = launches;

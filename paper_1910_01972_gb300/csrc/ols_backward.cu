@@ -11,61 +11,100 @@
 // non-overlapping) and the signal segment a = s[iL, iL+N):
 //   b_f  = g_f[iL, iL+L) zero-padded to N          B_f = FFT(b_f)
 //   A    = FFT(a)   (recomputed, never stored)
-//   dh_f^(i)[k] = IFFT(B_f conj(A))[(k + L) mod N]   (k < M: no wrap-around)
+//   dh_f[k] = sum_i IFFT(B_f^(i) conj(A^(i)))[(k + L) mod N]   (k < M: no wrap-around)
 //   ds over [iL, iL+N) = IFFT(sum_f B_f Ht_f),  Ht_f = FFT(conj(h_f[M-1-.]))/N
 // (the last is a linear convolution of support L + M - 1 = N, so no
-// aliasing).  2F + 2 FFTs per window.  Consecutive ds windows overlap by
-// M-1 samples: each window writes its exclusive middle [M-1, L) directly and
-// its first and last M-1 samples to a workspace; a second kernel adds the
-// overlaps.  dh is accumulated per (block, slot) over that slot's windows in
-// a workspace and summed by the second kernel in a fixed order with
-// compensated FP32 summation: the result is deterministic for a given plan
-// and device.
+// aliasing).  The inverse FFT is linear, so the sum over windows of dh is
+// taken in the frequency domain: each CTA accumulates
+// P_f = sum over its windows of B_f conj(A), and one inverse FFT per filter
+// at the end gives dh.  Per window that is F + 2 FFTs (A, the F gradient
+// windows, one inverse for ds) instead of the 2F + 2 of a per-window dh.
+//
+// Kernel shape: a CTA of BwdGeo::BLOCK threads holds BwdGeo::SLOTS windows
+// (one per N/16-thread slot); a slot's FFT exchanges synchronise that slot
+// only (named barrier), and once per filter the slots' products B_f conj(A)
+// are summed in shared memory in slot order and added to the CTA's P_f in
+// the workspace (L2-resident: grid x F x N complex).  Consecutive ds windows
+// overlap by M-1 samples: each window writes its exclusive middle [M-1, L)
+// directly and its first and last M-1 samples to a workspace; a second
+// kernel adds the overlaps and sums the CTAs' P_f in CTA order with
+// compensated FP32 summation; a third runs the F inverse FFTs.  The result
+// is deterministic for a given plan and device.
 #include <cuda_runtime.h>
 #include <cstdint>
 
 #include "ols_fft_passes.cuh"
 #include "ols_internal.h"
 
-#ifndef OLS_BWD_WARPS_PER_SM
-#define OLS_BWD_WARPS_PER_SM 8   // the adjoint keeps three spectra in registers: fewer, fatter warps
+#ifndef OLS_BWD_BLOCK
+#define OLS_BWD_BLOCK 512        // threads per adjoint CTA (slots of N/16 threads) ...
+#endif
+#ifndef OLS_BWD_BLOCK_MID
+#define OLS_BWD_BLOCK_MID 384    // ... except for N = 1024 and 2048 (measured)
+#endif
+#ifndef OLS_BWD_PREFETCH
+#define OLS_BWD_PREFETCH 1       // pull the next gradient window toward L2 while this one is transformed
+#endif
+#ifndef OLS_BWD_MINB
+#define OLS_BWD_MINB 1           // adjoint CTAs per SM the register budget must allow
 #endif
 
 namespace ols {
 
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// *p += v without waiting for the old value (an L2 reduction).  Only one
+// thread ever updates a given entry and its updates to one address are
+// applied in program order, so the sum is deterministic; IEEE round to
+// nearest like an FP32 add.
+__device__ __forceinline__ void red_add(float4 *p, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
 template <int LOG2N>
 struct BwdGeo {
-    static constexpr int MINB = (OLS_BWD_WARPS_PER_SM * 32 + Geo<LOG2N>::BLOCK - 1) / Geo<LOG2N>::BLOCK;
+    using G = Geo<LOG2N>;
+    static constexpr int TARGET = (G::T == 64 || G::T == 128) ? OLS_BWD_BLOCK_MID : OLS_BWD_BLOCK;
+    static constexpr int SLOTS = TARGET / G::T > 1 ? TARGET / G::T : 1;
+    static constexpr int BLOCK = SLOTS * G::T;
+    static_assert(SLOTS <= 15 || G::T <= 32, "one named barrier per slot");
+    static constexpr int HALF = G::N / 2;      // float4 entries of one spectrum
+    // exchange buffers of every slot, then one product buffer per slot (when SLOTS > 1)
+    static constexpr size_t XBYTES = sizeof(float2) * (size_t)SLOTS * G::XBUFS * G::PADN;
+    static constexpr size_t SMEM = XBYTES + (SLOTS > 1 ? sizeof(float4) * (size_t)SLOTS * HALF : 0);
 };
 
 template <int LOG2N, bool WANT_DS, bool WANT_DH>
-__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, BwdGeo<LOG2N>::MINB)
+__global__ void __launch_bounds__(BwdGeo<LOG2N>::BLOCK, OLS_BWD_MINB)
 ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *__restrict__ g,
                     long long Nout, const float4 *__restrict__ Htk, const float2 *__restrict__ twg,
-                    float2 *__restrict__ ds, float2 *__restrict__ edge, float2 *__restrict__ dh_part,
+                    float2 *__restrict__ ds, float2 *__restrict__ edge, float4 *__restrict__ P,
                     int M, int F, long long L, long long nseg) {
     using G = Geo<LOG2N>;
+    using BG = BwdGeo<LOG2N>;
     extern __shared__ float4 smem_raw[];
-    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
-    float2 *bufs = smem + G::TWN_PAD + slot * G::XBUFS * G::PADN;
-#if OLS_TW_GLOBAL
-    const float2 *tw = twg;
-#else
-    float2 *tw = smem;
-    for (int i = threadIdx.x; i < G::TWN; i += G::BLOCK) tw[i] = twg[i];
-    __syncthreads();
-#endif
+    float2 *bufs = reinterpret_cast<float2 *>(smem_raw) + slot * G::XBUFS * G::PADN;
+    float4 *prod = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES);
+    const SegmentBarrier<G::T> bar{1 + slot};
+    const TwGlobal tw{twg};
     const int lo = M - 1;
     const int Li = (int)L;
-    const float invN = 1.0f / (float)G::N;
-    float2 *dhp = WANT_DH ? dh_part + ((size_t)blockIdx.x * G::SEGS + slot) * (size_t)F * M : nullptr;
+    float4 *Pc = WANT_DH ? P + (size_t)blockIdx.x * F * BG::HALF : nullptr;
     int xc = 0;
-    const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
+    const long long nblk = (nseg + BG::SLOTS - 1) / BG::SLOTS;
     for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
         const bool first = blk == blockIdx.x;
-        const long long seg = blk * G::SEGS + slot;
+        const long long seg = blk * BG::SLOTS + slot;
         const bool active = seg < nseg;
         const long long start = active ? seg * L : 0;
 
@@ -76,7 +115,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
 #pragma unroll
             for (int k = 0; k < 16; ++k)
                 A[k] = (k * G::T + t < lim) ? __ldg(sig + start + k * G::T + t) : make_float2(0.f, 0.f);
-            forward_passes<LOG2N, 0>(A, bufs, tw, t, xc);
+            forward_passes<LOG2N, 0>(A, bufs, tw, t, xc, bar);
         }
         float2 D[16];
         if constexpr (WANT_DS) {
@@ -92,39 +131,61 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             const float2 *gf = g + (size_t)f * (size_t)Nout + start + t;
 #pragma unroll
             for (int k = 0; k < 16; ++k) b[k] = (k * G::T + t < gl) ? __ldg(gf + k * G::T) : make_float2(0.f, 0.f);
-            forward_passes<LOG2N, 0>(b, bufs, tw, t, xc);
+#if OLS_BWD_PREFETCH
+            // a window is at most N/16 = T lines of 128 B: one line per thread
+            if (f + 1 < F) {
+                if (t * 16 < gl) prefetch_l2(gf - t + Nout + t * 16);
+            } else {   // the last filter: the slot's next window (signal and first gradient row)
+                const long long nstart = (seg + (long long)gridDim.x * BG::SLOTS) * L + t * 16;
+                if (WANT_DH && nstart < Ns) prefetch_l2(sig + nstart);
+                if (nstart < Nout) prefetch_l2(g + nstart);
+            }
+#endif
+            forward_passes<LOG2N, 0>(b, bufs, tw, t, xc, bar);
             if constexpr (WANT_DS) {
-                const float4 *hp = Htk + (size_t)f * (G::N / 2) + t;
+                const float4 *hp = Htk + (size_t)f * BG::HALF + t;
 #pragma unroll
                 for (int j2 = 0; j2 < 8; ++j2) {
                     const float4 h = load_spectrum(hp + j2 * G::T);
-                    const float2 p0 = cmul(b[2 * j2], make_float2(h.x, h.y));
-                    const float2 p1 = cmul(b[2 * j2 + 1], make_float2(h.z, h.w));
-                    D[2 * j2] = cadd(D[2 * j2], p0);
-                    D[2 * j2 + 1] = cadd(D[2 * j2 + 1], p1);
+                    D[2 * j2] = cadd(D[2 * j2], cmul(b[2 * j2], make_float2(h.x, h.y)));
+                    D[2 * j2 + 1] = cadd(D[2 * j2 + 1], cmul(b[2 * j2 + 1], make_float2(h.z, h.w)));
                 }
             }
             if constexpr (WANT_DH) {
+                // B_f conj(A) at this thread's storage positions 16 t + j (entries j2 T + t)
+                float4 q[8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) b[j] = cmulc(b[j], A[j]);
-                inverse_passes<LOG2N, G::NP - 1>(b, bufs, tw, t, xc);
-                // b[k] holds c[n], n = k T + t;  dh_f[n - L] for n >= L, dh_f[M-1] for n = 0
-                float2 *dst = dhp + (size_t)f * M;
+                for (int j2 = 0; j2 < 8; ++j2) {
+                    const float2 q0 = cmulc(b[2 * j2], A[2 * j2]);
+                    const float2 q1 = cmulc(b[2 * j2 + 1], A[2 * j2 + 1]);
+                    q[j2] = make_float4(q0.x, q0.y, q1.x, q1.y);
+                }
+                float4 *Pf = Pc + (size_t)f * BG::HALF;
+                if constexpr (BG::SLOTS == 1) {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const int n = k * G::T + t;
-                    int kk = -1;
-                    if (n >= Li) kk = n - Li;
-                    else if (n == 0) kk = lo;
-                    if (active && kk >= 0) {
-                        const float2 v = make_float2(b[k].x * invN, b[k].y * invN);
-                        dst[kk] = first ? v : cadd(dst[kk], v);
+                    for (int j2 = 0; j2 < 8; ++j2) {
+                        float4 *dst = Pf + j2 * G::T + t;
+                        if (first) *dst = q[j2];
+                        else red_add(dst, q[j2]);
                     }
+                } else {
+                    // the slots' products summed in slot order, then added to the CTA's P_f
+#pragma unroll
+                    for (int j2 = 0; j2 < 8; ++j2) prod[slot * BG::HALF + j2 * G::T + t] = q[j2];
+                    __syncthreads();
+                    for (int e = threadIdx.x; e < BG::HALF; e += BG::BLOCK) {
+                        float4 acc = prod[e];
+#pragma unroll
+                        for (int s2 = 1; s2 < BG::SLOTS; ++s2) acc = f4add(acc, prod[s2 * BG::HALF + e]);
+                        if (first) Pf[e] = acc;
+                        else red_add(Pf + e, acc);
+                    }
+                    __syncthreads();
                 }
             }
         }
         if constexpr (WANT_DS) {
-            inverse_passes<LOG2N, G::NP - 1>(D, bufs, tw, t, xc);
+            inverse_passes<LOG2N, G::NP - 1>(D, bufs, tw, t, xc, bar);
             if (active) {
                 float2 *eh = edge + (size_t)seg * 2 * lo;      // head [0, lo), tail [lo, 2 lo)
 #pragma unroll
@@ -144,26 +205,32 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
 }
 
 // ds overlaps: ds[b L + u] = head_b[u] + tail_{b-1}[u] for b in [0, nseg],
-// u < M-1.  dh: compensated sum of the per-slot partials in slot order.
+// u < M-1.  dh spectra: Pr[e] = compensated sum of the CTAs' P[c][e] in CTA
+// order (e over F x N/2 float4 entries).
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+    const float y = v - c;
+    const float tt = s + y;
+    c = (tt - s) - y;
+    s = tt;
+}
+
 __global__ void ols_backward_finish_kernel(const float2 *__restrict__ edge, float2 *__restrict__ ds, long long Ns,
-                                           long long L, long long nseg, int M, const float2 *__restrict__ dh_part,
-                                           int npart, float2 *__restrict__ dh, int FM) {
+                                           long long L, long long nseg, int M, const float4 *__restrict__ P,
+                                           int npart, float4 *__restrict__ Pr, long long FH) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (dh && gid < FM) {
-        float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+    if (Pr && gid < FH) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
         for (int p = 0; p < npart; ++p) {
-            const float2 v = dh_part[(size_t)p * FM + gid];
-            const float yr = v.x - cr, yi = v.y - ci;
-            const float tr = sr + yr, ti = si + yi;
-            cr = (tr - sr) - yr;
-            ci = (ti - si) - yi;
-            sr = tr;
-            si = ti;
+            const float4 v = __ldcs(P + (size_t)p * FH + gid);
+            kahan_add(s0, c0, v.x);
+            kahan_add(s1, c1, v.y);
+            kahan_add(s2, c2, v.z);
+            kahan_add(s3, c3, v.w);
         }
-        dh[gid] = make_float2(sr, si);
+        Pr[gid] = make_float4(s0, s1, s2, s3);
         return;
     }
-    const long long e = gid - (dh ? FM : 0);
+    const long long e = gid - (Pr ? FH : 0);
     const int lo = M - 1;
     if (!ds || lo == 0 || e < 0 || e >= (nseg + 1) * (long long)lo) return;
     const long long b = e / lo;
@@ -179,15 +246,51 @@ __global__ void ols_backward_finish_kernel(const float2 *__restrict__ edge, floa
     ds[m] = v;
 }
 
+// dh_f[k] = IFFT(Pr_f)[(k + L) mod N] / N for k < M: one slot per filter.
+template <int LOG2N>
+__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK)
+ols_backward_dh_kernel(const float4 *__restrict__ Pr, const float2 *__restrict__ twg, float2 *__restrict__ dh,
+                       int M, int F, long long L) {
+    using G = Geo<LOG2N>;
+    extern __shared__ float4 smem_raw[];
+    const int slot = threadIdx.x / G::T;
+    const int t = threadIdx.x % G::T;
+    float2 *bufs = reinterpret_cast<float2 *>(smem_raw) + slot * G::XBUFS * G::PADN;
+    const int f = blockIdx.x * G::SEGS + slot;
+    const bool active = f < F;
+    float2 x[16];
+    const float4 *src = Pr + (size_t)(active ? f : 0) * (G::N / 2) + t;
+#pragma unroll
+    for (int j2 = 0; j2 < 8; ++j2) {
+        const float4 v = active ? src[j2 * G::T] : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[2 * j2] = make_float2(v.x, v.y);
+        x[2 * j2 + 1] = make_float2(v.z, v.w);
+    }
+    int xc = 0;
+    inverse_passes<LOG2N, G::NP - 1>(x, bufs, TwGlobal{twg}, t, xc);
+    if (!active) return;
+    const float invN = 1.0f / (float)G::N;
+    const int Li = (int)L;
+    float2 *dst = dh + (size_t)f * M;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int n = k * G::T + t;           // x[k] holds c[n]
+        int kk = -1;
+        if (n >= Li) kk = n - Li;
+        else if (n == 0) kk = M - 1;
+        if (kk >= 0) dst[kk] = make_float2(x[k].x * invN, x[k].y * invN);
+    }
+}
+
 template <int LOG2N, bool DS, bool DH>
 static cudaError_t prepare_bwd_one(ols_plan_s &p, int idx) {
-    using G = Geo<LOG2N>;
+    using BG = BwdGeo<LOG2N>;
     cudaError_t e = cudaFuncSetAttribute(ols_backward_kernel<LOG2N, DS, DH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_backward_kernel<LOG2N, DS, DH>, G::BLOCK,
-                                                      G::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_backward_kernel<LOG2N, DS, DH>, BG::BLOCK,
+                                                      BG::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     p.bwd_grid_cap[idx] = per_sm * p.sm_count;
@@ -199,6 +302,9 @@ static cudaError_t prepare_bwd_n(ols_plan_s &p) {
     cudaError_t e = prepare_bwd_one<LOG2N, true, true>(p, 0);
     if (e == cudaSuccess) e = prepare_bwd_one<LOG2N, true, false>(p, 1);
     if (e == cudaSuccess) e = prepare_bwd_one<LOG2N, false, true>(p, 2);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ols_backward_dh_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Geo<LOG2N>::SMEM);
     return e;
 }
 
@@ -216,12 +322,12 @@ cudaError_t prepare_backward(ols_plan_s &p) {
 
 int backward_segs_per_block(int log2N) {
     switch (log2N) {
-        case 8: return Geo<8>::SEGS;
-        case 9: return Geo<9>::SEGS;
-        case 10: return Geo<10>::SEGS;
-        case 11: return Geo<11>::SEGS;
-        case 12: return Geo<12>::SEGS;
-        case 13: return Geo<13>::SEGS;
+        case 8: return BwdGeo<8>::SLOTS;
+        case 9: return BwdGeo<9>::SLOTS;
+        case 10: return BwdGeo<10>::SLOTS;
+        case 11: return BwdGeo<11>::SLOTS;
+        case 12: return BwdGeo<12>::SLOTS;
+        case 13: return BwdGeo<13>::SLOTS;
         default: return 1;
     }
 }
@@ -235,10 +341,10 @@ int backward_grid(const ols_plan_s &p, int64_t nseg, bool want_ds, bool want_dh)
 
 template <int LOG2N, bool DS, bool DH>
 static void launch_bwd_one(const ols_plan_s &p, const BackwardArgs &a, cudaStream_t st) {
-    using G = Geo<LOG2N>;
-    ols_backward_kernel<LOG2N, DS, DH><<<a.grid, G::BLOCK, G::SMEM, st>>>(
-        a.s, a.Ns, a.g, a.Nout, reinterpret_cast<const float4 *>(p.Htk), p.tw, a.ds, a.edge, a.dh_part, p.M,
-        p.F, a.L, a.nseg);
+    using BG = BwdGeo<LOG2N>;
+    ols_backward_kernel<LOG2N, DS, DH><<<a.grid, BG::BLOCK, BG::SMEM, st>>>(
+        a.s, a.Ns, a.g, a.Nout, reinterpret_cast<const float4 *>(p.Htk), p.tw, a.ds, a.edge, a.P, p.M, p.F, a.L,
+        a.nseg);
 }
 
 template <int LOG2N>
@@ -246,6 +352,13 @@ static void launch_bwd_n(const ols_plan_s &p, const BackwardArgs &a, cudaStream_
     if (a.ds && a.dh) launch_bwd_one<LOG2N, true, true>(p, a, st);
     else if (a.ds) launch_bwd_one<LOG2N, true, false>(p, a, st);
     else launch_bwd_one<LOG2N, false, true>(p, a, st);
+}
+
+template <int LOG2N>
+static void launch_dh_n(const ols_plan_s &p, const BackwardArgs &a, cudaStream_t st) {
+    using G = Geo<LOG2N>;
+    const int grid = (p.F + G::SEGS - 1) / G::SEGS;
+    ols_backward_dh_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM, st>>>(a.Pr, p.tw, a.dh, p.M, p.F, a.L);
 }
 
 cudaError_t launch_backward(const ols_plan_s &p, const BackwardArgs &a, cudaStream_t st, int *launches) {
@@ -262,15 +375,29 @@ cudaError_t launch_backward(const ols_plan_s &p, const BackwardArgs &a, cudaStre
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *launches = 1;
-    const int FM = a.dh ? p.F * p.M : 0;
+    const long long FH = a.dh ? (long long)p.F * (p.N / 2) : 0;
     const long long nfix = a.ds ? (a.nseg + 1) * (long long)(p.M - 1) : 0;
-    const long long total = FM + nfix;
+    const long long total = FH + nfix;
     if (total > 0) {
         ols_backward_finish_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-            a.edge, a.ds, a.Ns, a.L, a.nseg, p.M, a.dh_part, a.npart, a.dh, FM);
+            a.edge, a.ds, a.Ns, a.L, a.nseg, p.M, a.P, a.grid, a.dh ? a.Pr : nullptr, FH);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         *launches = 2;
+    }
+    if (a.dh) {
+        switch (p.log2N) {
+            case 8: launch_dh_n<8>(p, a, st); break;
+            case 9: launch_dh_n<9>(p, a, st); break;
+            case 10: launch_dh_n<10>(p, a, st); break;
+            case 11: launch_dh_n<11>(p, a, st); break;
+            case 12: launch_dh_n<12>(p, a, st); break;
+            case 13: launch_dh_n<13>(p, a, st); break;
+            default: return cudaErrorInvalidValue;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        *launches = 3;
     }
     return cudaSuccess;
 }

@@ -91,14 +91,29 @@ __device__ __forceinline__ constexpr int pad_off(int k) {
     return k * s + ((k * s) >> 4);
 }
 
+// Barrier policies of an exchange: the whole CTA (kernels whose segments
+// advance in lock step), or only the NT threads of one segment (named
+// barrier `id`; a warp barrier when the segment fits in one warp).
+struct CtaBarrier {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+template <int NT>
+struct SegmentBarrier {
+    int id;
+    __device__ __forceinline__ void operator()() const {
+        if constexpr (NT <= 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NT) : "memory");
+    }
+};
+
 // Write x in the layout of pass PW, barrier, read it back in the layout of PR.
-template <int LOG2N, int PW, int PR>
-__device__ __forceinline__ void exchange(float2 *x, float2 *buf, int t) {
-    if constexpr (Geo<LOG2N>::XBUFS == 1) __syncthreads();   // previous readers of buf are done
+template <int LOG2N, int PW, int PR, class BAR = CtaBarrier>
+__device__ __forceinline__ void exchange(float2 *x, float2 *buf, int t, const BAR &bar = BAR{}) {
+    if constexpr (Geo<LOG2N>::XBUFS == 1) bar();   // previous readers of buf are done
     const int bw = pad_base<LOG2N, PW>(t);
 #pragma unroll
     for (int k = 0; k < 16; ++k) buf[bw + pad_off<LOG2N, PW>(k)] = x[k];
-    __syncthreads();
+    bar();
     const int br = pad_base<LOG2N, PR>(t);
 #pragma unroll
     for (int k = 0; k < 16; ++k) x[k] = buf[br + pad_off<LOG2N, PR>(k)];
@@ -214,17 +229,18 @@ __device__ __forceinline__ void twiddle(float2 *x, const float2 *tw, int t) {
     g.template apply<INV>(x, f);
 }
 
-template <int LOG2N, int P, class TW>
-__device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const TW &tw, int t, int &xc) {
+template <int LOG2N, int P, class TW, class BAR = CtaBarrier>
+__device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const TW &tw, int t, int &xc,
+                                               const BAR &bar = BAR{}) {
     using G = Geo<LOG2N>;
     if constexpr (P < G::NP - 1) {
         typename TW::Fetched f;
         tw.template fetch<LOG2N, P>(f, t);            // in flight during the DFT
         dft_groups<G::radix(P), false>(x);
         tw.template apply<false>(x, f);
-        exchange<LOG2N, P, P + 1>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
+        exchange<LOG2N, P, P + 1>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t, bar);
         ++xc;
-        forward_passes<LOG2N, P + 1>(x, bufs, tw, t, xc);
+        forward_passes<LOG2N, P + 1>(x, bufs, tw, t, xc, bar);
     } else {
         dft_groups<G::radix(P), false>(x);
     }
@@ -236,18 +252,19 @@ __device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const fl
 
 // x holds pass P+1's layout (or pass NP-1's when P == NP-1); runs the
 // inverse of passes P, P-1, ..., 0.
-template <int LOG2N, int P, class TW>
-__device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const TW &tw, int t, int &xc) {
+template <int LOG2N, int P, class TW, class BAR = CtaBarrier>
+__device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const TW &tw, int t, int &xc,
+                                               const BAR &bar = BAR{}) {
     using G = Geo<LOG2N>;
     if constexpr (P < G::NP - 1) {
         typename TW::Fetched f;
         tw.template fetch<LOG2N, P>(f, t);            // in flight during the exchange
-        exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
+        exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t, bar);
         ++xc;
         tw.template apply<true>(x, f);
     }
     dft_groups<G::radix(P), true>(x);
-    if constexpr (P > 0) inverse_passes<LOG2N, P - 1>(x, bufs, tw, t, xc);
+    if constexpr (P > 0) inverse_passes<LOG2N, P - 1>(x, bufs, tw, t, xc, bar);
 }
 template <int LOG2N, int P>
 __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc) {

@@ -83,8 +83,9 @@ struct BackwardArgs {
     const float2 *g;
     int64_t Nout, L, nseg;
     float2 *ds, *dh;
-    float2 *edge, *dh_part;   // workspace parts
-    int grid, npart;
+    float2 *edge;             // workspace: ds overlap edges (nseg x 2 x (M-1))
+    float4 *P, *Pr;           // workspace: per-CTA dh spectra (grid x F x N/2), their sum (F x N/2)
+    int grid;
 };
 
 // One problem of a batch, as the batched kernel reads it.

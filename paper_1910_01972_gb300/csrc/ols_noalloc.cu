@@ -2,7 +2,7 @@
 // that cannot allocate device memory.
 //
 // ols_convolve_backward needs a scratch workspace (the ds overlap edges and
-// the per-slot dh partials).  Some callers cannot provide one: real-time
+// the per-CTA dh spectra).  Some callers cannot provide one: real-time
 // signal-processing pipelines that forbid any allocation once they are
 // running (cudaMalloc can block and synchronise the device, which breaks
 // their latency budget), and host programs that own every device allocation
