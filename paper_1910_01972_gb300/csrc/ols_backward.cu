@@ -37,16 +37,16 @@
 #include "ols_internal.h"
 
 #ifndef OLS_BWD_BLOCK
-#define OLS_BWD_BLOCK 512        // threads per adjoint CTA (slots of N/16 threads) ...
+#define OLS_BWD_BLOCK 512        // threads per adjoint CTA (slots of N/16 threads), one CTA per SM ...
 #endif
-#ifndef OLS_BWD_BLOCK_MID
-#define OLS_BWD_BLOCK_MID 384    // ... except for N = 1024 and 2048 (measured)
+#ifndef OLS_BWD_BLOCK_1024
+#define OLS_BWD_BLOCK_1024 256   // ... except for N = 1024: two CTAs of 256 per SM (measured)
+#endif
+#ifndef OLS_BWD_MINB_1024
+#define OLS_BWD_MINB_1024 2
 #endif
 #ifndef OLS_BWD_PREFETCH
 #define OLS_BWD_PREFETCH 1       // pull the next gradient window toward L2 while this one is transformed
-#endif
-#ifndef OLS_BWD_MINB
-#define OLS_BWD_MINB 1           // adjoint CTAs per SM the register budget must allow
 #endif
 
 namespace ols {
@@ -72,18 +72,20 @@ __device__ __forceinline__ void red_add(float4 *p, float4 v) {
 template <int LOG2N>
 struct BwdGeo {
     using G = Geo<LOG2N>;
-    static constexpr int TARGET = (G::T == 64 || G::T == 128) ? OLS_BWD_BLOCK_MID : OLS_BWD_BLOCK;
+    static constexpr int TARGET = G::T == 64 ? OLS_BWD_BLOCK_1024 : OLS_BWD_BLOCK;
+    static constexpr int MINB = G::T == 64 ? OLS_BWD_MINB_1024 : 1;   // CTAs per SM for the register budget
     static constexpr int SLOTS = TARGET / G::T > 1 ? TARGET / G::T : 1;
     static constexpr int BLOCK = SLOTS * G::T;
     static_assert(SLOTS <= 15 || G::T <= 32, "one named barrier per slot");
     static constexpr int HALF = G::N / 2;      // float4 entries of one spectrum
-    // exchange buffers of every slot, then one product buffer per slot (when SLOTS > 1)
+    // exchange buffers of every slot, then each slot's signal spectrum A
     static constexpr size_t XBYTES = sizeof(float2) * (size_t)SLOTS * G::XBUFS * G::PADN;
-    static constexpr size_t SMEM = XBYTES + (SLOTS > 1 ? sizeof(float4) * (size_t)SLOTS * HALF : 0);
+    static constexpr size_t SMEM = XBYTES + sizeof(float4) * (size_t)SLOTS * HALF;
+    static_assert(G::XBUFS == 2, "the product buffer is the exchange buffer not in use");
 };
 
 template <int LOG2N, bool WANT_DS, bool WANT_DH>
-__global__ void __launch_bounds__(BwdGeo<LOG2N>::BLOCK, OLS_BWD_MINB)
+__global__ void __launch_bounds__(BwdGeo<LOG2N>::BLOCK, BwdGeo<LOG2N>::MINB)
 ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *__restrict__ g,
                     long long Nout, const float4 *__restrict__ Htk, const float2 *__restrict__ twg,
                     float2 *__restrict__ ds, float2 *__restrict__ edge, float4 *__restrict__ P,
@@ -93,8 +95,9 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
     extern __shared__ float4 smem_raw[];
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
-    float2 *bufs = reinterpret_cast<float2 *>(smem_raw) + slot * G::XBUFS * G::PADN;
-    float4 *prod = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES);
+    float2 *const xbase = reinterpret_cast<float2 *>(smem_raw);
+    float2 *bufs = xbase + slot * G::XBUFS * G::PADN;
+    float4 *Asm = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES) + slot * BG::HALF;
     const SegmentBarrier<G::T> bar{1 + slot};
     const TwGlobal tw{twg};
     const int lo = M - 1;
@@ -108,14 +111,18 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
         const bool active = seg < nseg;
         const long long start = active ? seg * L : 0;
 
-        float2 A[16];
         if constexpr (WANT_DH) {
+            float2 A[16];
             const long long avail = active ? (Ns - start) : 0;
             const int lim = (int)(avail < G::N ? avail : G::N);
 #pragma unroll
             for (int k = 0; k < 16; ++k)
                 A[k] = (k * G::T + t < lim) ? __ldg(sig + start + k * G::T + t) : make_float2(0.f, 0.f);
             forward_passes<LOG2N, 0>(A, bufs, tw, t, xc, bar);
+            // kept in shared memory (the thread's own entries) rather than 32 registers
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2)
+                Asm[j2 * G::T + t] = make_float4(A[2 * j2].x, A[2 * j2].y, A[2 * j2 + 1].x, A[2 * j2 + 1].y);
         }
         float2 D[16];
         if constexpr (WANT_DS) {
@@ -156,8 +163,9 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
                 float4 q[8];
 #pragma unroll
                 for (int j2 = 0; j2 < 8; ++j2) {
-                    const float2 q0 = cmulc(b[2 * j2], A[2 * j2]);
-                    const float2 q1 = cmulc(b[2 * j2 + 1], A[2 * j2 + 1]);
+                    const float4 a = Asm[j2 * G::T + t];
+                    const float2 q0 = cmulc(b[2 * j2], make_float2(a.x, a.y));
+                    const float2 q1 = cmulc(b[2 * j2 + 1], make_float2(a.z, a.w));
                     q[j2] = make_float4(q0.x, q0.y, q1.x, q1.y);
                 }
                 float4 *Pf = Pc + (size_t)f * BG::HALF;
@@ -169,14 +177,19 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
                         else red_add(dst, q[j2]);
                     }
                 } else {
-                    // the slots' products summed in slot order, then added to the CTA's P_f
+                    // the slots' products summed in slot order, then added to the CTA's P_f.
+                    // Staged in each slot's exchange buffer that the next exchange writes
+                    // (xc & 1): its last readers are past this FFT's final exchange, and
+                    // its next writer comes after the second barrier below.
+                    float4 *prod = reinterpret_cast<float4 *>(xbase + (xc & 1) * G::PADN);
+                    constexpr int SSTRIDE = G::XBUFS * G::PADN / 2;   // float4 between slots
 #pragma unroll
-                    for (int j2 = 0; j2 < 8; ++j2) prod[slot * BG::HALF + j2 * G::T + t] = q[j2];
+                    for (int j2 = 0; j2 < 8; ++j2) prod[slot * SSTRIDE + j2 * G::T + t] = q[j2];
                     __syncthreads();
                     for (int e = threadIdx.x; e < BG::HALF; e += BG::BLOCK) {
                         float4 acc = prod[e];
 #pragma unroll
-                        for (int s2 = 1; s2 < BG::SLOTS; ++s2) acc = f4add(acc, prod[s2 * BG::HALF + e]);
+                        for (int s2 = 1; s2 < BG::SLOTS; ++s2) acc = f4add(acc, prod[s2 * SSTRIDE + e]);
                         if (first) Pf[e] = acc;
                         else red_add(Pf + e, acc);
                     }

@@ -93,7 +93,8 @@ __device__ __forceinline__ constexpr int pad_off(int k) {
 
 // Barrier policies of an exchange: the whole CTA (kernels whose segments
 // advance in lock step), or only the NT threads of one segment (named
-// barrier `id`; a warp barrier when the segment fits in one warp).
+// barrier `id`; a warp barrier over the segment's lanes when it fits in one
+// warp, so segments sharing a warp may follow different paths).
 struct CtaBarrier {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
@@ -101,8 +102,14 @@ template <int NT>
 struct SegmentBarrier {
     int id;
     __device__ __forceinline__ void operator()() const {
-        if constexpr (NT <= 32) __syncwarp();
-        else asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NT) : "memory");
+        if constexpr (NT < 32) {
+            const unsigned lane = threadIdx.x & 31u;
+            __syncwarp(((1u << NT) - 1u) << (lane & ~(unsigned)(NT - 1)));
+        } else if constexpr (NT == 32) {
+            __syncwarp();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NT) : "memory");
+        }
     }
 };
 
