@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ns", type=int, default=0, help="override the signal length (profiling a smaller case)")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads (batched, adjoint, tensor-core)")
+    ap.add_argument("--only", choices=["plain_1x1", "diff", "batched", "tensor_core"], default=None,
+                    help="run just this other workload (with --ns: its signal length) and print its numbers")
     return ap.parse_args()
 
 
@@ -220,17 +222,35 @@ def _time_events(fn, reps, flush=None):
     return tot / reps
 
 
-def measure_others(peak):
+def measure_others(peak, only=None, ns=0):
     """Throughput of the other workloads on this GPU (outputs and samples for
-    oracle checks are returned separately; the oracle runs in the CPU leg)."""
-    import numpy as np
+    oracle checks are returned separately; the oracle runs in the CPU leg).
+    `only` restricts the run to one workload (for profiling); `ns` then
+    overrides the differentiable workload's signal length."""
     import torch
-    import synth
-    from paper_1910_01972_gb300 import BatchPlan, Plan, _native
     res, samples = {}, {}
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")       # 256 MB > L2
 
+    def want(name):
+        return only is None or only == name
+
     # one signal, one filter (65,536 samples, M = 64, N = 512): fits in L2, so flush between calls
+    if want("plain_1x1"):
+        _plain_1x1(res, flush)
+    if want("diff"):
+        _diff(res, samples, peak, ns)
+    if want("batched"):
+        _batched(res, samples, peak)
+    if want("tensor_core"):
+        _tensor_core(res, samples, peak)
+    torch.cuda.empty_cache()
+    return res, samples
+
+
+def _plain_1x1(res, flush):
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import Plan
     cfg = synth.PLAIN_1x1
     s_np, h_np = synth.plain_inputs(cfg)
     p = Plan(cfg.M, cfg.F, cfg.N)
@@ -243,8 +263,16 @@ def measure_others(peak):
                         "note": "L2 flushed between calls; launch-latency bound (146 segments)"}
     p.close()
 
-    # differentiable shape: forward + adjoint (ds and dh)
+
+def _diff(res, samples, peak, ns):
+    """Differentiable shape: forward + adjoint (ds and dh)."""
+    import dataclasses
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import Plan, _native
     cfg = synth.DIFF
+    if ns:
+        cfg = dataclasses.replace(cfg, Ns=ns, name=cfg.name.replace("Ns4194304", "Ns%d" % ns))
     s_np, h_np, w_np = synth.diff_inputs(cfg)
     p = Plan(cfg.M, cfg.F, cfg.N)
     p.set_filters(torch.from_numpy(h_np).cuda())
@@ -274,7 +302,13 @@ def measure_others(peak):
     p.close()
     del y, gy, ds, dh, ws
 
-    # uneven batch: one graph replay of the batched launches vs 64 per-signal plain launches
+
+def _batched(res, samples, peak):
+    """Uneven batch: one graph replay of the batched launches vs 64 per-signal plain launches."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import BatchPlan, Plan
     spec = synth.batch_spec()
     ss, hs = synth.batch_inputs(spec)
     bp = BatchPlan(spec.Ns, spec.M, spec.F)
@@ -327,7 +361,13 @@ def measure_others(peak):
     bp.close()
     del ys, sd, graph
 
-    # tensor-core split precision vs FP32 on the same inputs
+
+def _tensor_core(res, samples, peak):
+    """Tensor-core split precision vs FP32 on the same inputs."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import Plan, _native
     cfg = synth.TC_SPLIT
     s_np, h_np = synth.plain_inputs(cfg)
     s = torch.from_numpy(s_np).cuda()
@@ -353,8 +393,6 @@ def measure_others(peak):
         q.close()
     res["tensor_core"] = {"workload": cfg.name, **tcres}
     del y, s, h
-    torch.cuda.empty_cache()
-    return res, samples
 
 
 def others_errors(samples):
@@ -398,6 +436,15 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     _native.lib()
+    if args.only:
+        # one other workload alone (profiling aid): its numbers, no headline line
+        if rank == 0:
+            peak, _ = measured_peaks()
+            res, _ = measure_others(peak, only=args.only, ns=args.ns)
+            print(json.dumps({"only": args.only, "others": res}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
 
     cfg = synth.PLAIN_BANK
     if args.ns:

@@ -45,6 +45,9 @@
 #ifndef OLS_BWD_MINB_1024
 #define OLS_BWD_MINB_1024 2
 #endif
+#ifndef OLS_BWD_L2HINTS
+#define OLS_BWD_L2HINTS 1        // streamed s and g loads evict first, the per-CTA dh spectra evict last
+#endif
 #ifndef OLS_BWD_PREFETCH
 #define OLS_BWD_PREFETCH 1       // pull the next gradient window toward L2 while this one is transformed
 #endif
@@ -59,14 +62,58 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// L2 eviction priorities: the signal and gradient are read once and stream
+// through L2 (evict first); the CTAs' dh spectra (grid x F x N complex) are
+// updated once per window and should stay resident (evict last).
+struct L2Hints {
+    uint64_t stream, keep;
+    __device__ __forceinline__ static L2Hints make() {
+        L2Hints h;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(h.stream));
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(h.keep));
+        return h;
+    }
+};
+
+__device__ __forceinline__ float2 ld_stream(const float2 *p, const L2Hints &h) {
+#if OLS_BWD_L2HINTS
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(p), "l"(h.stream));
+    return v;
+#else
+    (void)h;
+    return __ldg(p);
+#endif
+}
+
 // *p += v without waiting for the old value (an L2 reduction).  Only one
 // thread ever updates a given entry and its updates to one address are
 // applied in program order, so the sum is deterministic; IEEE round to
 // nearest like an FP32 add.
-__device__ __forceinline__ void red_add(float4 *p, float4 v) {
+__device__ __forceinline__ void red_add(float4 *p, float4 v, const L2Hints &h) {
+#if OLS_BWD_L2HINTS
+    asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(h.keep)
+                 : "memory");
+#else
+    (void)h;
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
                  "f"(v.w)
                  : "memory");
+#endif
+}
+
+__device__ __forceinline__ void st_keep(float4 *p, float4 v, const L2Hints &h) {
+#if OLS_BWD_L2HINTS
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(h.keep)
+                 : "memory");
+#else
+    (void)h;
+    *p = v;
+#endif
 }
 
 template <int LOG2N>
@@ -100,6 +147,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
     float4 *Asm = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES) + slot * BG::HALF;
     const SegmentBarrier<G::T> bar{1 + slot};
     const TwGlobal tw{twg};
+    const L2Hints l2 = L2Hints::make();
     const int lo = M - 1;
     const int Li = (int)L;
     float4 *Pc = WANT_DH ? P + (size_t)blockIdx.x * F * BG::HALF : nullptr;
@@ -117,7 +165,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             const int lim = (int)(avail < G::N ? avail : G::N);
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                A[k] = (k * G::T + t < lim) ? __ldg(sig + start + k * G::T + t) : make_float2(0.f, 0.f);
+                A[k] = (k * G::T + t < lim) ? ld_stream(sig + start + k * G::T + t, l2) : make_float2(0.f, 0.f);
             forward_passes<LOG2N, 0>(A, bufs, tw, t, xc, bar);
             // kept in shared memory (the thread's own entries) rather than 32 registers
 #pragma unroll
@@ -137,7 +185,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             float2 b[16];
             const float2 *gf = g + (size_t)f * (size_t)Nout + start + t;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) b[k] = (k * G::T + t < gl) ? __ldg(gf + k * G::T) : make_float2(0.f, 0.f);
+            for (int k = 0; k < 16; ++k) b[k] = (k * G::T + t < gl) ? ld_stream(gf + k * G::T, l2) : make_float2(0.f, 0.f);
 #if OLS_BWD_PREFETCH
             // a window is at most N/16 = T lines of 128 B: one line per thread
             if (f + 1 < F) {
@@ -173,8 +221,8 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
 #pragma unroll
                     for (int j2 = 0; j2 < 8; ++j2) {
                         float4 *dst = Pf + j2 * G::T + t;
-                        if (first) *dst = q[j2];
-                        else red_add(dst, q[j2]);
+                        if (first) st_keep(dst, q[j2], l2);
+                        else red_add(dst, q[j2], l2);
                     }
                 } else {
                     // the slots' products summed in slot order, then added to the CTA's P_f.
@@ -190,8 +238,8 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
                         float4 acc = prod[e];
 #pragma unroll
                         for (int s2 = 1; s2 < BG::SLOTS; ++s2) acc = f4add(acc, prod[s2 * SSTRIDE + e]);
-                        if (first) Pf[e] = acc;
-                        else red_add(Pf + e, acc);
+                        if (first) st_keep(Pf + e, acc, l2);
+                        else red_add(Pf + e, acc, l2);
                     }
                     __syncthreads();
                 }
@@ -218,8 +266,8 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
 }
 
 // ds overlaps: ds[b L + u] = head_b[u] + tail_{b-1}[u] for b in [0, nseg],
-// u < M-1.  dh spectra: Pr[e] = compensated sum of the CTAs' P[c][e] in CTA
-// order (e over F x N/2 float4 entries).
+// u < M-1.  dh spectra: Pr[e] = compensated sum of the CTAs' P[c][e] in a
+// fixed order (e over F x N/2 float4 entries).
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
     const float y = v - c;
     const float tt = s + y;
@@ -227,23 +275,44 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
     s = tt;
 }
 
-__global__ void ols_backward_finish_kernel(const float2 *__restrict__ edge, float2 *__restrict__ ds, long long Ns,
-                                           long long L, long long nseg, int M, const float4 *__restrict__ P,
-                                           int npart, float4 *__restrict__ Pr, long long FH) {
+constexpr int kFinishLanes = 8;   // threads per dh spectrum entry in the finishing sum
+
+__global__ void __launch_bounds__(256)
+ols_backward_finish_kernel(const float2 *__restrict__ edge, float2 *__restrict__ ds, long long Ns, long long L,
+                           long long nseg, int M, const float4 *__restrict__ P, int npart,
+                           float4 *__restrict__ Pr, long long FH) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (Pr && gid < FH) {
+    const long long nred = Pr ? FH * kFinishLanes : 0;
+    if (gid < nred) {
+        // lane r of entry e sums the partials p = r, r + 8, ... (compensated); the
+        // 8 lanes' sums are then added in lane order, also compensated
+        const long long e = gid / kFinishLanes;
+        const int r = (int)(gid % kFinishLanes);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-        for (int p = 0; p < npart; ++p) {
-            const float4 v = __ldcs(P + (size_t)p * FH + gid);
+#pragma unroll 4
+        for (int p = r; p < npart; p += kFinishLanes) {
+            const float4 v = __ldcs(P + (size_t)p * FH + e);
             kahan_add(s0, c0, v.x);
             kahan_add(s1, c1, v.y);
             kahan_add(s2, c2, v.z);
             kahan_add(s3, c3, v.w);
         }
-        Pr[gid] = make_float4(s0, s1, s2, s3);
+        // the 8 lanes of an entry are consecutive threads of one warp (nred is a
+        // multiple of 8 and warps start at multiples of 32)
+        const unsigned base = threadIdx.x & 31u & ~(unsigned)(kFinishLanes - 1);
+        const unsigned grp = ((1u << kFinishLanes) - 1u) << base;
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+        for (int q = 0; q < kFinishLanes; ++q) {
+            const int src = (int)base + q;
+            kahan_add(t0, d0, __shfl_sync(grp, s0, src) - __shfl_sync(grp, c0, src));
+            kahan_add(t1, d1, __shfl_sync(grp, s1, src) - __shfl_sync(grp, c1, src));
+            kahan_add(t2, d2, __shfl_sync(grp, s2, src) - __shfl_sync(grp, c2, src));
+            kahan_add(t3, d3, __shfl_sync(grp, s3, src) - __shfl_sync(grp, c3, src));
+        }
+        if (r == 0) Pr[e] = make_float4(t0, t1, t2, t3);
         return;
     }
-    const long long e = gid - (Pr ? FH : 0);
+    const long long e = gid - nred;
     const int lo = M - 1;
     if (!ds || lo == 0 || e < 0 || e >= (nseg + 1) * (long long)lo) return;
     const long long b = e / lo;
@@ -390,7 +459,7 @@ cudaError_t launch_backward(const ols_plan_s &p, const BackwardArgs &a, cudaStre
     *launches = 1;
     const long long FH = a.dh ? (long long)p.F * (p.N / 2) : 0;
     const long long nfix = a.ds ? (a.nseg + 1) * (long long)(p.M - 1) : 0;
-    const long long total = FH + nfix;
+    const long long total = FH * kFinishLanes + nfix;
     if (total > 0) {
         ols_backward_finish_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
             a.edge, a.ds, a.Ns, a.L, a.nseg, p.M, a.P, a.grid, a.dh ? a.Pr : nullptr, FH);
