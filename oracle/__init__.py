@@ -58,6 +58,10 @@ def _load():
         lib.ols_oracle_conv_at.restype = ctypes.c_int
         lib.ols_oracle_adjoint.argtypes = [i64, vp, i32, i32, vp, vp, vp, vp]
         lib.ols_oracle_adjoint.restype = ctypes.c_int
+        lib.ols_oracle_conv_real.argtypes = [i64, vp, i32, i32, vp, vp]
+        lib.ols_oracle_conv_real.restype = ctypes.c_int
+        lib.ols_oracle_conv_real_at.argtypes = [i64, vp, i32, i32, vp, i64, vp, vp, vp]
+        lib.ols_oracle_conv_real_at.restype = ctypes.c_int
         lib.ols_oracle_threads.argtypes = []
         lib.ols_oracle_threads.restype = ctypes.c_int
         lib.ols_oracle_set_threads.argtypes = [ctypes.c_int]
@@ -123,6 +127,51 @@ def conv_at(s, h, f_idx, j_idx) -> np.ndarray:
                                     _ptr(fi), _ptr(ji), _ptr(out))
     if rc != 0:
         raise ValueError("ols_oracle_conv_at rejected the sizes or an index")
+    return out
+
+
+def _f32(a) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.float32:
+        raise TypeError("real oracle inputs are float32 (the FP32 values the GPU consumes), got %s" % a.dtype)
+    return a
+
+
+def conv_real(s, h) -> np.ndarray:
+    """Real valid-mode convolution y[F][Ns-M+1] (float64) of real s[Ns] with
+    real h[F][M] (the R2R form); ``h`` may be 1-D."""
+    s = _f32(s)
+    h = _f32(h)
+    squeeze = h.ndim == 1
+    if squeeze:
+        h = h[None, :]
+    F, M = h.shape
+    Ns = s.shape[0]
+    if M < 1 or F < 1 or Ns < M:
+        raise ValueError("need M >= 1, F >= 1, Ns >= M")
+    y = np.empty((F, Ns - M + 1), dtype=np.float64)
+    rc = _load().ols_oracle_conv_real(Ns, _ptr(s), M, F, _ptr(h), _ptr(y))
+    if rc != 0:
+        raise ValueError("ols_oracle_conv_real rejected the sizes")
+    return y[0] if squeeze else y
+
+
+def conv_real_at(s, h, f_idx, j_idx) -> np.ndarray:
+    """Real y_{f_idx[i]}[j_idx[i]] for each i (float64)."""
+    s = _f32(s)
+    h = _f32(h)
+    if h.ndim == 1:
+        h = h[None, :]
+    F, M = h.shape
+    fi = np.ascontiguousarray(f_idx, dtype=np.int64)
+    ji = np.ascontiguousarray(j_idx, dtype=np.int64)
+    if fi.shape != ji.shape:
+        raise ValueError("index arrays differ in shape")
+    out = np.empty(fi.shape, dtype=np.float64)
+    rc = _load().ols_oracle_conv_real_at(s.shape[0], _ptr(s), M, F, _ptr(h), fi.size,
+                                         _ptr(fi), _ptr(ji), _ptr(out))
+    if rc != 0:
+        raise ValueError("ols_oracle_conv_real_at rejected the sizes or an index")
     return out
 
 

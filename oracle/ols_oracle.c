@@ -31,6 +31,10 @@
  *
  * where g_f[j] = dL/dRe y_f[j] + i dL/dIm y_f[j].
  *
+ * The paper's second variant (Sec. 3.3, the R2R SM-OLS) convolves a real
+ * signal with real filters; its exact result is the same valid part of Eq. 1
+ * on real data, computed here separately in real FP64 (ols_oracle_conv_real).
+ *
  * Layouts: every complex array is interleaved (re, im) pairs.  s[Ns] and
  * h[F][M] are FP32 (as the GPU consumes them); g[F][Nout] and every output
  * are FP64.  Parallelism: OpenMP over independent output elements only; each
@@ -169,5 +173,48 @@ int ols_oracle_adjoint(int64_t Ns, const float *s, int32_t M, int32_t F,
             dh[2 * idx + 1] = acc_im;
         }
     }
+    return 0;
+}
+
+/* One output of Eq. 1 (valid part) on real data: y_f[j]. */
+static double conv_one_real(const float *s, int32_t M, const float *hf, int64_t j)
+{
+    double acc = 0.0;
+    for (int32_t k = 0; k < M; ++k)
+        acc += (double)s[j + (int64_t)M - 1 - k] * (double)hf[k];
+    return acc;
+}
+
+/*
+ * Real-to-real valid-mode convolution for a bank of F filters (Eq. 1 on real
+ * data, the R2R form of Sec. 3.3).  s: [Ns] real (FP32), h: [F][M] real
+ * (FP32), y: [F][Ns-M+1] real (FP64).  Returns 0, or -1 on invalid sizes.
+ */
+int ols_oracle_conv_real(int64_t Ns, const float *s, int32_t M, int32_t F,
+                         const float *h, double *y)
+{
+    if (M < 1 || F < 1 || Ns < M) return -1;
+    const int64_t Nout = Ns - M + 1;
+    const int64_t total = (int64_t)F * Nout;
+    int64_t idx;
+#pragma omp parallel for schedule(static)
+    for (idx = 0; idx < total; ++idx)
+        y[idx] = conv_one_real(s, M, h + (size_t)(idx / Nout) * M, idx % Nout);
+    return 0;
+}
+
+/* Selected outputs of the real convolution: out[i] = y_{fi[i]}[ji[i]]. */
+int ols_oracle_conv_real_at(int64_t Ns, const float *s, int32_t M, int32_t F,
+                            const float *h, int64_t n, const int64_t *fi,
+                            const int64_t *ji, double *out)
+{
+    if (M < 1 || F < 1 || Ns < M) return -1;
+    const int64_t Nout = Ns - M + 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (fi[i] < 0 || fi[i] >= F || ji[i] < 0 || ji[i] >= Nout) return -1;
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i)
+        out[i] = conv_one_real(s, M, h + (size_t)fi[i] * M, ji[i]);
     return 0;
 }

@@ -249,3 +249,63 @@ def pin_adjoint_finite_difference(conv, adjoint, seed=17, Ns=4096, F=16, M=129,
 
 QUICK_PINS = (pin_golden_conv, pin_golden_adjoint, pin_bruteforce_dft, pin_delta_shift,
               pin_linearity, pin_closed_forms, pin_adjoint_dot)
+
+
+# ------------------------------------------------------ real-to-real (R2R) form
+# The paper's second OLS variant (Sec. 3.3) convolves real signals with real
+# filters; its exact result is Eq. 1's valid part on real data.  Each pin
+# takes conv_real(s, h) -> y (float64) on float32 inputs.
+
+def pin_real_bruteforce(conv_real, seed=21):
+    """Against numpy's direct 'valid' convolution in FP64 (np.convolve flips h,
+    as Eq. 1 does), over shapes including M = 1 and M = Ns."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    for (Ns, M, F) in ((1, 1, 1), (40, 1, 2), (64, 7, 3), (37, 37, 2), (300, 33, 2), (129, 64, 1)):
+        s = g.uniform(-1, 1, Ns).astype(np.float32)
+        h = g.normal(size=(F, M)).astype(np.float32)
+        y = conv_real(s, h)
+        for f in range(F):
+            ref = np.convolve(s.astype(np.float64), h[f].astype(np.float64), mode="valid")
+            assert y[f].shape == ref.shape
+            assert np.max(np.abs(y[f] - ref)) <= 1e-13 * (np.max(np.abs(ref)) + 1.0), (Ns, M, f)
+
+
+def pin_real_delta_shift(conv_real, seed=22):
+    """h = e_d gives y[j] = s[j + M - 1 - d], exactly."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    s = g.uniform(-1, 1, 300).astype(np.float32)
+    for M in (1, 2, 5, 64):
+        for d in sorted({0, M // 2, M - 1}):
+            h = np.zeros(M, np.float32)
+            h[d] = 1
+            assert np.array_equal(conv_real(s, h), s[M - 1 - d: len(s) - d].astype(np.float64)), (M, d)
+
+
+def pin_real_closed_forms(conv_real, seed=23):
+    """A constant signal gives sum_k h[k]; s[n] = (-1)^n gives
+    (-1)^(j+M-1) sum_k (-1)^k h[k] (both exact sums of FP32 taps in FP64
+    up to rounding of the reference)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    Ns, M = 257, 13
+    h = g.normal(size=M).astype(np.float32)
+    hd = h.astype(np.float64)
+    j = np.arange(Ns - M + 1)
+    y = conv_real(np.ones(Ns, np.float32), h)
+    assert np.max(np.abs(y - hd.sum())) < 1e-12
+    alt = ((-1.0) ** np.arange(Ns)).astype(np.float32)
+    ref = ((-1.0) ** (j + M - 1)) * np.sum(hd * (-1.0) ** np.arange(M))
+    assert np.max(np.abs(conv_real(alt, h) - ref)) < 1e-12
+
+
+def pin_real_is_complex_on_real_data(conv_real, conv, seed=24):
+    """On real data the complex oracle's sums reduce term by term to the real
+    ones (every imaginary product is an exact zero), so the real parts agree
+    bit for bit and the imaginary parts are zero."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    s = g.uniform(-1, 1, 500).astype(np.float32)
+    h = g.normal(size=(3, 41)).astype(np.float32)
+    yc = conv(s.astype(np.complex64), h.astype(np.complex64))
+    assert np.array_equal(yc.real, conv_real(s, h)) and not np.any(yc.imag)
+
+
+REAL_QUICK_PINS = (pin_real_bruteforce, pin_real_delta_shift, pin_real_closed_forms)

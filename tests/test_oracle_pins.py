@@ -27,6 +27,29 @@ def test_oracle_pin(pin):
     pin(_conv, _adj)
 
 
+@pytest.mark.parametrize("pin", P.REAL_QUICK_PINS)
+def test_oracle_real_pin(pin):
+    pin(oracle.conv_real)
+
+
+def test_oracle_real_matches_complex_on_real_data():
+    P.pin_real_is_complex_on_real_data(oracle.conv_real, oracle.conv)
+
+
+def test_oracle_conv_real_at_matches_conv_real():
+    g = np.random.Generator(np.random.PCG64(5))
+    s = g.uniform(-1, 1, 900).astype(np.float32)
+    h = g.normal(size=(3, 20)).astype(np.float32)
+    y = oracle.conv_real(s, h)
+    fi = g.integers(0, 3, 100)
+    ji = g.integers(0, y.shape[1], 100)
+    assert np.array_equal(oracle.conv_real_at(s, h, fi, ji), y[fi, ji])
+    with pytest.raises(TypeError):
+        oracle.conv_real(s.astype(np.float64), h)
+    with pytest.raises(ValueError):
+        oracle.conv_real(s[:5], h)
+
+
 def test_oracle_adjoint_finite_difference():
     worst = P.pin_adjoint_finite_difference(_conv, _adj)
     assert worst < 1e-9
@@ -139,3 +162,49 @@ def test_pins_catch_planted_mistake(name):
             except AssertionError:
                 caught.append(pin.__name__)
         assert caught, "no pin caught mutant " + name
+
+
+REAL_MUTANTS = {
+    "real_drop_last_tap": ("for (int32_t k = 0; k < M; ++k)\n        acc += (double)s[j + (int64_t)M - 1 - k]",
+                           "for (int32_t k = 0; k < M - 1; ++k)\n        acc += (double)s[j + (int64_t)M - 1 - k]"),
+    "real_off_by_one": ("acc += (double)s[j + (int64_t)M - 1 - k] * (double)hf[k];",
+                        "acc += (double)s[j + (int64_t)M - 1 - k + (k > 0)] * (double)hf[k];"),
+    "real_unflipped": ("acc += (double)s[j + (int64_t)M - 1 - k] * (double)hf[k];",
+                       "acc += (double)s[j + k] * (double)hf[k];"),
+}
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(REAL_MUTANTS))
+def test_real_pins_catch_planted_mistake(name):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "ols_oracle.c")).read()
+    old, new = REAL_MUTANTS[name]
+    assert src.count(old) == 1, "mutation anchor not unique: " + name
+    with tempfile.TemporaryDirectory() as d:
+        cpath = os.path.join(d, "mut.c")
+        with open(cpath, "w") as fh:
+            fh.write(src.replace(old, new))
+        so = os.path.join(d, "libmut.so")
+        subprocess.run(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                        "-std=c11", "-o", so, cpath], check=True)
+        lib = ctypes.CDLL(so)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.ols_oracle_conv_real.argtypes = [i64, vp, i32, i32, vp, vp]
+
+        def conv_real(s, h):
+            s = np.ascontiguousarray(s, np.float32)
+            h = np.ascontiguousarray(h, np.float32)
+            sq = h.ndim == 1
+            h2 = h[None] if sq else h
+            F, M = h2.shape
+            y = np.empty((F, len(s) - M + 1), np.float64)
+            lib.ols_oracle_conv_real(len(s), s.ctypes.data, M, F, h2.ctypes.data, y.ctypes.data)
+            return y[0] if sq else y
+
+        caught = []
+        for pin in P.REAL_QUICK_PINS:
+            try:
+                pin(conv_real)
+            except AssertionError:
+                caught.append(pin.__name__)
+        assert caught, "planted mistake %s passed every real pin" % name
