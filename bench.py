@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ns", type=int, default=0, help="override the signal length (profiling a smaller case)")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads (batched, adjoint, tensor-core)")
-    ap.add_argument("--only", choices=["plain_1x1", "diff", "batched", "tensor_core"], default=None,
+    ap.add_argument("--only", choices=["plain_1x1", "diff", "batched", "tensor_core", "r2r"], default=None,
                     help="run just this other workload (with --ns: its signal length) and print its numbers")
     return ap.parse_args()
 
@@ -243,6 +243,8 @@ def measure_others(peak, only=None, ns=0):
         _batched(res, samples, peak)
     if want("tensor_core"):
         _tensor_core(res, samples, peak)
+    if want("r2r"):
+        _r2r(res, samples, peak)
     torch.cuda.empty_cache()
     return res, samples
 
@@ -395,6 +397,34 @@ def _tensor_core(res, samples, peak):
     del y, s, h
 
 
+def _r2r(res, samples, peak):
+    """Real-to-real form (Sec. 3.3's R2R variant) on the filter-bank shape."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import Plan, _native
+    cfg = synth.R2R_BANK
+    s_np, h_np = synth.real_inputs(cfg)
+    p = Plan(cfg.M, cfg.F, cfg.N, flags=_native.OLS_FLAG_R2R)
+    p.set_filters_real(torch.from_numpy(h_np).cuda())
+    s = torch.from_numpy(s_np).cuda()
+    y = p.convolve_real(s)
+    ms = _time_events(lambda: p.convolve_real(s, out=y), 20)
+    nout = cfg.Ns - cfg.M + 1
+    fc = (cfg.F + 1) // 2
+    rb = 4 * cfg.Ns + 8 * fc * cfg.N + 4 * cfg.F * nout
+    res["r2r"] = {"workload": cfg.name, "value": cfg.F * nout / (ms * 1e-3), "unit": "real " + UNIT, "ms": ms,
+                  "hbm_frac": rb / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": rb,
+                  "note": "real signal and filters; filters paired into one complex inverse FFT each"}
+    g = np.random.Generator(np.random.PCG64(9))
+    fi = g.integers(0, cfg.F, 4000)
+    ji = g.integers(0, nout, 4000)
+    samples["r2r"] = {"s": s_np, "h": h_np, "fi": fi, "ji": ji,
+                      "got": y[torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()].cpu().numpy()}
+    p.close()
+    del y, s
+
+
 def others_errors(samples):
     """Relative L2 errors of the other workloads' sampled outputs against the oracle."""
     import numpy as np
@@ -407,6 +437,10 @@ def others_errors(samples):
             num += float(np.sum(np.abs(got - ref) ** 2))
             den += float(np.sum(np.abs(ref) ** 2))
         out["batched"] = (num / den) ** 0.5
+    if samples.get("r2r"):
+        d = samples["r2r"]
+        ref = oracle.conv_real_at(d["s"], d["h"], d["fi"], d["ji"])
+        out["r2r"] = float(np.linalg.norm(d["got"].astype(np.float64) - ref) / np.linalg.norm(ref))
     if samples.get("tc"):
         d = samples["tc"]
         ref = oracle.conv_at(d["s"], d["h"], d["fi"], d["ji"])

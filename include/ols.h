@@ -77,6 +77,11 @@ typedef struct ols_batch_s *ols_batch_t;
  * overflow).  Forward convolution only (ols_convolve, ols_convolve_host). */
 #define OLS_FLAG_TC_FP16SPLIT 1u
 #define OLS_FLAG_TC_BF16SPLIT 2u
+/* Real-to-real convolution (Sec. 3.3's R2R variant and Algorithm 2 with
+ * real input): real signal, F real filters, real outputs, FP32.  Such a plan
+ * serves only ols_set_filters_real / ols_convolve_real (and the host-side
+ * queries); the complex entry points return OLS_ERR_UNSUPPORTED for it. */
+#define OLS_FLAG_R2R 4u
 
 /* Human-readable name of a status code (static storage; never NULL). */
 OLS_API const char *ols_status_string(int status);
@@ -110,7 +115,8 @@ OLS_API int ols_spectrum_order(int64_t N, int32_t *nu);
  * (Sec. 3.2; N = 0 lets the library pick N from M, F and the segment-length
  * rule of Sec. 5: each N is best for a range of M).  Allocates the plan's
  * device tables (filter spectra F*N complex, twiddles) on the current
- * device.  flags: OLS_FLAG_FP32, OLS_FLAG_TC_FP16SPLIT or OLS_FLAG_TC_BF16SPLIT.
+ * device.  flags: OLS_FLAG_FP32, OLS_FLAG_TC_FP16SPLIT, OLS_FLAG_TC_BF16SPLIT
+ * or OLS_FLAG_R2R (real data; ceil(F/2) complex spectra).
  * Errors: INVALID (out == NULL, M < 1, F < 1), UNSUPPORTED (N, M > N, flags),
  * CUDA / ALLOC from the device.  *out is NULL on error.
  */
@@ -155,6 +161,34 @@ OLS_API int ols_get_spectra(ols_plan_t plan, float *H, void *stream);
  * filters), CUDA (launch failure).
  */
 OLS_API int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream);
+
+/*
+ * Filter spectra of a real-to-real plan (flags OLS_FLAG_R2R).  h: device
+ * [F][M] real FP32 (4-byte aligned).  The filters are taken in pairs as the
+ * complex sequences g_p = h_{2p} + i h_{2p+1}, p < ceil(F/2) (the partner of
+ * the last filter of an odd bank is zero), and each g_p is zero-padded and
+ * transformed as in ols_set_filters (FP64, 1/N folded in, rounded to FP32,
+ * kernel order).  ols_get_spectra then returns these ceil(F/2) spectra.
+ * Errors: INVALID (plan or h NULL / misaligned), UNSUPPORTED (not an R2R
+ * plan), CUDA.
+ */
+OLS_API int ols_set_filters_real(ols_plan_t plan, const float *h, void *stream);
+
+/*
+ * Real-to-real fused OLS convolution (Sec. 3.3's R2R variant; Eq. 1 on real
+ * data, valid part):  y_f[j] = sum_k s[j+M-1-k] h_f[k],  j < Ns-M+1.
+ * s: device [Ns] real FP32; y: device [F][Ns-M+1] real FP32 (row f = filter
+ * f); both 4-byte aligned, not overlapping.  One kernel: each segment of s is
+ * read once and transformed once (as a complex sequence with zero imaginary
+ * part); for each filter pair p one inverse FFT of the product with the
+ * spectrum of g_p gives s*h_{2p} in its real part and s*h_{2p+1} in its
+ * imaginary part (both convolutions are real), so each inverse FFT serves two
+ * output streams.  The paper's R2R kernel instead uses half-length
+ * transforms with real/complex post-processing; the outputs are the same.
+ * Errors: INVALID (NULL / misaligned pointer, Ns < M), UNSUPPORTED (not an
+ * R2R plan), NOT_READY (no filters), CUDA (launch failure).
+ */
+OLS_API int ols_convolve_real(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream);
 
 /*
  * The same convolution with HOST buffers (what a user outside the device

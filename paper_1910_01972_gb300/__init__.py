@@ -33,6 +33,17 @@ def _require(t: torch.Tensor, name: str, device=None):
         raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
 
 
+def _require_real(t: torch.Tensor, name: str, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.dtype != torch.float32:
+        raise TypeError("%s must be float32, got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
+
+
 def geometry(N: int, M: int, Ns: int):
     """(L, nseg, Nout) of Sec. 3.2's segmentation; host arithmetic only."""
     rc, L, nseg, Nout = _native.ols_geometry(N, M, Ns)
@@ -114,6 +125,33 @@ class Plan:
                 raise ValueError("out must have shape [F][Ns-M+1]")
         check(_native.ols_convolve(self._h, s.data_ptr(), Ns, out.data_ptr(), _stream_ptr(self.device)),
               "ols_convolve")
+        return out
+
+    def set_filters_real(self, h: torch.Tensor) -> None:
+        """Real-to-real plans (flags=OLS_FLAG_R2R): h [F][M] float32 on the plan's device."""
+        _require_real(h, "h", self.device)
+        if tuple(h.shape) != (self.F, self.M):
+            raise ValueError("h must have shape [%d][%d]" % (self.F, self.M))
+        check(_native.ols_set_filters_real(self._h, h.data_ptr(), _stream_ptr(self.device)), "ols_set_filters_real")
+        self._filters = h
+
+    def convolve_real(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Real valid-mode convolution: s [Ns] float32 -> y [F][Ns-M+1] float32 (R2R plans)."""
+        _require_real(s, "s", self.device)
+        if s.dim() != 1:
+            raise ValueError("s must be 1-D")
+        Ns = s.shape[0]
+        if Ns < self.M:
+            raise ValueError("signal shorter than the filter (Ns < M)")
+        Nout = Ns - self.M + 1
+        if out is None:
+            out = torch.empty((self.F, Nout), dtype=torch.float32, device=self.device)
+        else:
+            _require_real(out, "out", self.device)
+            if tuple(out.shape) != (self.F, Nout):
+                raise ValueError("out must have shape [F][Ns-M+1]")
+        check(_native.ols_convolve_real(self._h, s.data_ptr(), Ns, out.data_ptr(), _stream_ptr(self.device)),
+              "ols_convolve_real")
         return out
 
     def convolve_host(self, s_host: torch.Tensor, out_host: torch.Tensor | None = None) -> torch.Tensor:

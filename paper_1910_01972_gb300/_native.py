@@ -29,6 +29,7 @@ OLS_FLAG_FP32 = 0
 OLS_TUNE_MODEL = 1 << 8
 OLS_FLAG_TC_FP16SPLIT = 1
 OLS_FLAG_TC_BF16SPLIT = 2
+OLS_FLAG_R2R = 4
 
 # (name, restype, argtypes) of every exported symbol declared in include/ols.h
 i32, i64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
@@ -46,6 +47,8 @@ SIGNATURES = [
     ("ols_get_spectra", cint, [vp, vp, vp]),
     ("ols_convolve", cint, [vp, vp, i64, vp, vp]),
     ("ols_convolve_host", cint, [vp, vp, i64, vp, vp]),
+    ("ols_set_filters_real", cint, [vp, vp, vp]),
+    ("ols_convolve_real", cint, [vp, vp, i64, vp, vp]),
     ("ols_backward_workspace", cint, [vp, i64, cint, cint, ctypes.POINTER(ctypes.c_size_t)]),
     ("ols_convolve_backward", cint, [vp, vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     ("ols_convolve_backward_noalloc", cint, [vp, vp, i64, vp, vp, vp, vp]),
@@ -141,6 +144,14 @@ def ols_get_spectra(plan, H_ptr: int, stream: int) -> int:
 
 def ols_convolve(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
     return lib().ols_convolve(plan, s_ptr, Ns, y_ptr, stream)
+
+
+def ols_set_filters_real(plan, h_ptr: int, stream: int) -> int:
+    return lib().ols_set_filters_real(plan, h_ptr, stream)
+
+
+def ols_convolve_real(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
+    return lib().ols_convolve_real(plan, s_ptr, Ns, y_ptr, stream)
 
 
 def ols_convolve_host(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:

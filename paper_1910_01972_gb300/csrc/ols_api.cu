@@ -198,6 +198,7 @@ static void free_plan(ols_plan_s *p) {
     if (p->tc_bmat) cudaFree(p->tc_bmat);
     if (p->Hk_w64) cudaFree(p->Hk_w64);
     if (p->tw_pair) cudaFree(p->tw_pair);
+    if (p->hpack) cudaFree(p->hpack);
     if (p->tw_w64) cudaFree(p->tw_w64);
     if (p->nu_w64) cudaFree(p->nu_w64);
     if (p->d_status) cudaFree(p->d_status);
@@ -252,7 +253,8 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     if (!out) return OLS_ERR_INVALID;
     *out = nullptr;
     if (M < 1 || F < 1) return OLS_ERR_INVALID;
-    if (flags != OLS_FLAG_FP32 && flags != OLS_FLAG_TC_FP16SPLIT && flags != OLS_FLAG_TC_BF16SPLIT)
+    if (flags != OLS_FLAG_FP32 && flags != OLS_FLAG_TC_FP16SPLIT && flags != OLS_FLAG_TC_BF16SPLIT &&
+        flags != OLS_FLAG_R2R)
         return OLS_ERR_UNSUPPORTED;
     if (N == 0) N = choose_segment_length(M);
     const int l = log2_exact(N);
@@ -268,8 +270,12 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     p->pp = make_pass_plan(l);
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
-    if (e == cudaSuccess) e = cudaMalloc(&p->Hk, sizeof(float2) * (size_t)F * (size_t)N);
-    if (e == cudaSuccess) e = cudaMalloc(&p->Htk, sizeof(float2) * (size_t)F * (size_t)N);
+    const bool r2r = flags == OLS_FLAG_R2R;
+    const int32_t Fc = r2r ? (F + 1) / 2 : F;       // complex spectra held: paired filters for R2R
+    if (e == cudaSuccess) e = cudaMalloc(&p->Hk, sizeof(float2) * (size_t)Fc * (size_t)N);
+    if (e == cudaSuccess && !r2r) e = cudaMalloc(&p->Htk, sizeof(float2) * (size_t)F * (size_t)N);
+    if (e == cudaSuccess && r2r) e = cudaMalloc(&p->hpack, sizeof(float2) * (size_t)Fc * (size_t)M);
+    if (e == cudaSuccess && r2r) e = r2r_prepare(*p);
     if (e == cudaSuccess) e = cudaMalloc(&p->tw, sizeof(float2) * (size_t)(p->pp.twn > 0 ? p->pp.twn : 1));
     if (e == cudaSuccess) e = cudaMalloc(&p->tw64, sizeof(double2) * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc(&p->nu, sizeof(int32_t) * (size_t)N);
@@ -344,6 +350,7 @@ int ols_plan_query(ols_plan_t plan, int64_t Ns, int64_t *N, int32_t *M, int32_t 
 
 int ols_set_filters(ols_plan_t plan, const float *h, void *stream) {
     if (!plan || !h || !aligned8(h)) return OLS_ERR_INVALID;
+    if (plan->flags == OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
     const float2 *hh = reinterpret_cast<const float2 *>(h);
     cudaError_t e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0, 0,
                                    (cudaStream_t)stream);
@@ -361,12 +368,14 @@ int ols_set_filters(ols_plan_t plan, const float *h, void *stream) {
 int ols_get_spectra(ols_plan_t plan, float *H, void *stream) {
     if (!plan || !H || !aligned8(H)) return OLS_ERR_INVALID;
     if (!plan->filters_ready) return OLS_ERR_NOT_READY;
-    return status_of(launch_spectra_natural(plan->Hk, plan->F, plan->log2N, plan->nu,
+    const int Fc = plan->flags == OLS_FLAG_R2R ? (plan->F + 1) / 2 : plan->F;
+    return status_of(launch_spectra_natural(plan->Hk, Fc, plan->log2N, plan->nu,
                                             reinterpret_cast<float2 *>(H), (cudaStream_t)stream));
 }
 
 int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream) {
     if (!plan || !s || !y || !aligned8(s) || !aligned8(y)) return OLS_ERR_INVALID;
+    if (plan->flags == OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
     if (!plan->filters_ready) return OLS_ERR_NOT_READY;
     int64_t L, nseg, Nout;
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
@@ -378,8 +387,36 @@ int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *st
     return status_of(e);
 }
 
+static bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
+
+int ols_set_filters_real(ols_plan_t plan, const float *h, void *stream) {
+    if (!plan || !h || !aligned4(h)) return OLS_ERR_INVALID;
+    if (plan->flags != OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
+    const int Fc = (plan->F + 1) / 2;
+    cudaError_t e = launch_pack_real_pairs(h, plan->M, plan->F, plan->hpack, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = launch_spectra(plan->hpack, plan->M, Fc, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0, 0,
+                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return status_of(e);
+    plan->filters_ready = true;
+    return OLS_OK;
+}
+
+int ols_convolve_real(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream) {
+    if (!plan || !s || !y || !aligned4(s) || !aligned4(y)) return OLS_ERR_INVALID;
+    if (plan->flags != OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
+    if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    int64_t L, nseg, Nout;
+    int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
+    if (rc != OLS_OK) return rc;
+    cudaError_t e = r2r_launch(*plan, s, Ns, y, L, nseg, Nout, (cudaStream_t)stream);
+    plan->last_launches = 1;
+    return status_of(e);
+}
+
 int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y_host, void *stream) {
     if (!plan || !s_host || !y_host || !aligned8(s_host) || !aligned8(y_host)) return OLS_ERR_INVALID;
+    if (plan->flags == OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
     if (!plan->filters_ready) return OLS_ERR_NOT_READY;
     int64_t L, nseg, Nout;
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);

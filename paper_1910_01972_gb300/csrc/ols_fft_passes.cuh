@@ -28,7 +28,7 @@
 #define OLS_PREFETCH_H 1     // load filter f+1's spectrum while filter f is transformed
 #endif
 #ifndef OLS_H_L2ONLY
-#define OLS_H_L2ONLY 0       // 1: spectra bypass L1 (__ldcg) instead of __ldg
+#define OLS_H_L2ONLY 0       // 1: spectra bypass L1 (__ldcg), 2: not allocated in L1, instead of __ldg
 #endif
 #ifndef OLS_XBUFS
 #define OLS_XBUFS 2          // exchange buffers per segment (2: one barrier per exchange)
@@ -279,7 +279,13 @@ __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const fl
 }
 
 __device__ __forceinline__ float4 load_spectrum(const float4 *p) {
-#if OLS_H_L2ONLY
+#if OLS_H_L2ONLY == 2
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+#elif OLS_H_L2ONLY
     return __ldcg(p);
 #else
     return __ldg(p);

@@ -70,6 +70,9 @@ struct ols_plan_s {
     // two-segments-per-thread kernel (N >= 2048)
     float4 *tw_pair = nullptr;   // twiddle table as broadcast pairs (wr, wr, wi, wi)
     int pair_grid_cap = 0;
+    // real-to-real plans (OLS_FLAG_R2R)
+    float2 *hpack = nullptr;     // [ceil(F/2)][M] paired real filters h_{2p} + i h_{2p+1}
+    int r2r_grid_cap = 0;
     uint16_t *tc_bmat = nullptr; // split DFT-16 matrices (fwd hi, fwd lo, inv hi, inv lo), core-matrix layout
     int *d_status = nullptr;     // device status word (bounded-wait failures)
     ols::Staging stage;
@@ -119,6 +122,12 @@ void spectral_order_w64(int32_t *nu);
 cudaError_t pair_prepare(ols_plan_s &p);
 cudaError_t pair_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
                         int64_t Nout, cudaStream_t st);
+
+// Real-to-real form (ols_r2r.cu): filters paired as h_{2p} + i h_{2p+1}.
+cudaError_t launch_pack_real_pairs(const float *h, int M, int F, float2 *g, cudaStream_t st);
+cudaError_t r2r_prepare(ols_plan_s &p);
+cudaError_t r2r_launch(const ols_plan_s &p, const float *s, int64_t Ns, float *y, int64_t L, int64_t nseg,
+                       int64_t Nout, cudaStream_t st);
 
 // Tensor-core split-precision form (ols_tc.cu).
 cudaError_t tc_prepare(ols_plan_s &p, bool bf16);

@@ -20,9 +20,16 @@
 
 #include "ols_fft_passes.cuh"
 #include "ols_internal.h"
+#include "tmem.cuh"
 
 #ifndef OLS_PAIR_WARPS_PER_SM
 #define OLS_PAIR_WARPS_PER_SM 8  // resident warps per SM the register budget must allow
+#endif
+#ifndef OLS_PAIR_XBUFS
+#define OLS_PAIR_XBUFS 2         // exchange buffers (1: an extra barrier per exchange, half the shared memory)
+#endif
+#ifndef OLS_PAIR_X_TMEM
+#define OLS_PAIR_X_TMEM 0        // 1: the segment spectra wait in TMEM between filters, not in registers
 #endif
 
 namespace ols {
@@ -34,7 +41,7 @@ struct PGeo {
     static_assert(G::T >= 128, "pair kernel needs one segment per 128-thread multiple");
     static constexpr int BLOCK = G::T;
     static constexpr int MINB = (OLS_PAIR_WARPS_PER_SM * 32 + BLOCK - 1) / BLOCK;
-    static constexpr size_t SMEM = sizeof(float4) * 2 * (size_t)G::PADN;   // two exchange buffers
+    static constexpr size_t SMEM = sizeof(float4) * OLS_PAIR_XBUFS * (size_t)G::PADN;   // exchange buffers
 };
 
 __device__ __forceinline__ float4 pack(const cpair &c) { return make_float4(c.re.x, c.re.y, c.im.x, c.im.y); }
@@ -42,6 +49,7 @@ __device__ __forceinline__ cpair unpack(float4 v) { return {make_float2(v.x, v.y
 
 template <int LOG2N, int PW, int PR>
 __device__ __forceinline__ void exchange(cpair *x, float4 *buf, int t) {
+    if constexpr (OLS_PAIR_XBUFS == 1) __syncthreads();   // previous readers of buf are done
     const int bw = pad_base<LOG2N, PW>(t);
 #pragma unroll
     for (int k = 0; k < 16; ++k) buf[bw + pad_off<LOG2N, PW>(k)] = pack(x[k]);
@@ -95,7 +103,7 @@ __device__ __forceinline__ void forward_passes(cpair *x, float4 *bufs, const TwP
         tw.template fetch<LOG2N, P>(f, t);
         dft_groups<G::radix(P), false>(x);
         tw.template apply<false>(x, f);
-        exchange<LOG2N, P, P + 1>(x, bufs + (xc & 1) * G::PADN, t);
+        exchange<LOG2N, P, P + 1>(x, bufs + (OLS_PAIR_XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
         ++xc;
         forward_passes<LOG2N, P + 1>(x, bufs, tw, t, xc);
     } else {
@@ -109,7 +117,7 @@ __device__ __forceinline__ void inverse_passes(cpair *x, float4 *bufs, const TwP
     if constexpr (P < G::NP - 1) {
         TwPair::Fetched f;
         tw.template fetch<LOG2N, P>(f, t);
-        exchange<LOG2N, P + 1, P>(x, bufs + (xc & 1) * G::PADN, t);
+        exchange<LOG2N, P + 1, P>(x, bufs + (OLS_PAIR_XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
         ++xc;
         tw.template apply<true>(x, f);
     }
@@ -130,6 +138,15 @@ ols_pair_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
     const pairk::TwPair tw{twp};
     const int lo = M - 1;
     int xc = 0;
+#if OLS_PAIR_X_TMEM
+    // 64 TMEM columns per CTA: thread t's lane holds its 16 spectrum pairs.
+    __shared__ uint32_t tbase;
+    if (threadIdx.x < 32) tmem::alloc(&tbase, 64);
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    const uint32_t xcol = tbase + tmem::lane_bits();
+#endif
     const long long npair = (nseg + 1) / 2;
     for (long long pi = blockIdx.x; pi < npair; pi += gridDim.x) {
         const long long sa = 2 * pi, sb = 2 * pi + 1;
@@ -151,6 +168,11 @@ ols_pair_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
             }
         }
         pairk::forward_passes<LOG2N, 0>(X, smem4, tw, t, xc);
+#if OLS_PAIR_X_TMEM
+        tmem::st32(xcol, reinterpret_cast<const float *>(X));
+        tmem::st32(xcol + 32, reinterpret_cast<const float *>(X + 8));
+        tmem::wait_st();
+#endif
 
         const long long rem_a = Nout - start_a, rem_b = act_b ? Nout - start_b : 0;
         const int span_a = (int)(rem_a < (long long)(G::N - lo) ? rem_a : (long long)(G::N - lo));
@@ -162,10 +184,18 @@ ols_pair_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
         for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
         for (int f = 0; f < F; ++f) {
             cpair x[16];
+#if OLS_PAIR_X_TMEM
+            tmem::ld32(xcol, reinterpret_cast<float *>(x));
+            tmem::ld32(xcol + 32, reinterpret_cast<float *>(x + 8));
+            tmem::wait_ld();
+#else
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = X[j];
+#endif
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2) {
-                x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].x), make_float2(hn[j2].y, hn[j2].y));
-                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].z), make_float2(hn[j2].w, hn[j2].w));
+                x[2 * j2] = cmul(x[2 * j2], make_float2(hn[j2].x, hn[j2].x), make_float2(hn[j2].y, hn[j2].y));
+                x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].z), make_float2(hn[j2].w, hn[j2].w));
             }
             if (f + 1 < F) {
                 const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
@@ -182,6 +212,12 @@ ols_pair_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
             }
         }
     }
+#if OLS_PAIR_X_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, 64);
+#endif
 }
 
 template <int LOG2N>

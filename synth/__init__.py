@@ -15,7 +15,9 @@ and filter banks of stated sizes), so every workload here is synthetic:
   optionally times a symmetric Hann window 0.5(1 - cos(2 pi k/(M-1))), then
   scaled to unit L2 norm per filter;
 * loss weights: uniform[0, 1], one weight per output index shared by all
-  filters.
+  filters;
+* real-to-real workloads: signal i.i.d. uniform[-1, 1], filter taps i.i.d.
+  N(0, 1) (optionally Hann-windowed), unit L2 per filter.
 """
 from __future__ import annotations
 
@@ -59,6 +61,22 @@ def filters(g: np.random.Generator, F: int, M: int, window: bool = False) -> np.
     return (h / nrm).astype(np.complex64)
 
 
+def real_signal(g: np.random.Generator, Ns: int) -> np.ndarray:
+    """float32 real signal, i.i.d. uniform[-1, 1]."""
+    return g.uniform(-1.0, 1.0, size=Ns).astype(np.float32)
+
+
+def real_filters(g: np.random.Generator, F: int, M: int, window: bool = False) -> np.ndarray:
+    """float32 real filter bank [F][M]: i.i.d. N(0, 1) taps (optionally times
+    the symmetric Hann window), unit L2 per filter."""
+    h = g.normal(0.0, 1.0, size=(F, M))
+    if window:
+        h = h * hann(M)[None, :]
+    nrm = np.linalg.norm(h, axis=1, keepdims=True)
+    nrm[nrm == 0] = 1.0
+    return (h / nrm).astype(np.float32)
+
+
 def weights(g: np.random.Generator, n: int) -> np.ndarray:
     """Loss weights w[n] ~ uniform[0, 1] (float32)."""
     return g.uniform(0.0, 1.0, size=n).astype(np.float32)
@@ -84,6 +102,18 @@ PLAIN_1x1 = Plain("plain_1x1_Ns65536_M64_N512", 65536, 1, 64, 512, False, 0)
 PLAIN_BANK = Plain("bank_Ns8388608_F32_M257_N2048", 1 << 23, 32, 257, 2048, True, 1)
 DIFF = Plain("diff_Ns4194304_F16_M129_N1024", 1 << 22, 16, 129, 1024, False, 3)
 TC_SPLIT = Plain("tc_Ns16777216_F64_M512_N4096", 1 << 24, 64, 512, 4096, False, 4)
+
+
+# real-to-real form (Sec. 3.3's R2R variant) on the filter-bank shape
+R2R_BANK = Plain("r2r_bank_Ns8388608_F32_M257_N2048", 1 << 23, 32, 257, 2048, True, 5)
+
+
+def real_inputs(cfg: Plain, Ns: int | None = None):
+    """(s, h) float32 for a real-to-real workload; ``Ns`` overrides the signal length."""
+    g = rng(cfg.index)
+    s = real_signal(g, cfg.Ns if Ns is None else Ns)
+    h = real_filters(g, cfg.F, cfg.M, window=cfg.window)
+    return s, h
 
 
 def plain_inputs(cfg: Plain, Ns: int | None = None):
