@@ -6,9 +6,11 @@ legs of ``bench.py`` may import this package.  The product library
 
 The arithmetic lives in ``ols_oracle.c`` (plain C, FP64, OpenMP over output
 elements): the valid part of Eq. 1 for a bank of filters (Sec. 3.2 states
-that OLS returns exactly this, whatever the segment length), and the adjoint
-of that linear map.  This module only compiles the C file and marshals numpy
-arrays through ctypes.
+that OLS returns exactly this, whatever the segment length), the adjoint
+of that linear map, the real-to-real form, and the post-processing of the
+output (power, and the derivative read as central differences with
+one-sided ends, Sec. 4.3); ``detect`` only selects from ``power``.  This
+module only compiles the C file and marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
 
@@ -62,6 +64,12 @@ def _load():
         lib.ols_oracle_conv_real.restype = ctypes.c_int
         lib.ols_oracle_conv_real_at.argtypes = [i64, vp, i32, i32, vp, i64, vp, vp, vp]
         lib.ols_oracle_conv_real_at.restype = ctypes.c_int
+        lib.ols_oracle_power.argtypes = [i64, vp, i32, i32, vp, vp]
+        lib.ols_oracle_power.restype = ctypes.c_int
+        lib.ols_oracle_derivative.argtypes = [i64, vp, i32, i32, vp, vp]
+        lib.ols_oracle_derivative.restype = ctypes.c_int
+        lib.ols_oracle_derivative_at.argtypes = [i64, vp, i32, i32, vp, i64, vp, vp, vp]
+        lib.ols_oracle_derivative_at.restype = ctypes.c_int
         lib.ols_oracle_threads.argtypes = []
         lib.ols_oracle_threads.restype = ctypes.c_int
         lib.ols_oracle_set_threads.argtypes = [ctypes.c_int]
@@ -172,6 +180,67 @@ def conv_real_at(s, h, f_idx, j_idx) -> np.ndarray:
                                          _ptr(fi), _ptr(ji), _ptr(out))
     if rc != 0:
         raise ValueError("ols_oracle_conv_real_at rejected the sizes or an index")
+    return out
+
+
+def _bank(s, h):
+    s = _c64(s)
+    h = _c64(h)
+    squeeze = h.ndim == 1
+    if squeeze:
+        h = h[None, :]
+    F, M = h.shape
+    if M < 1 or F < 1 or s.shape[0] < M:
+        raise ValueError("need M >= 1, F >= 1, Ns >= M")
+    return s, h, F, M, squeeze
+
+
+def power(s, h) -> np.ndarray:
+    """Power of the convolved output, p[F][Ns-M+1] = |y|^2 (float64)."""
+    s, h, F, M, squeeze = _bank(s, h)
+    p = np.empty((F, s.shape[0] - M + 1), dtype=np.float64)
+    if _load().ols_oracle_power(s.shape[0], _ptr(s), M, F, _ptr(h), _ptr(p)) != 0:
+        raise ValueError("ols_oracle_power rejected the sizes")
+    return p[0] if squeeze else p
+
+
+def power_at(s, h, f_idx, j_idx) -> np.ndarray:
+    """|y_{f_idx[i]}[j_idx[i]]|^2 (float64)."""
+    y = conv_at(s, h, f_idx, j_idx)
+    return y.real * y.real + y.imag * y.imag
+
+
+def detect(s, h, threshold: float):
+    """Candidates of the power detector: the set of (f, j) with
+    |y_f[j]|^2 >= threshold, and their powers (float64)."""
+    p = power(s, h)
+    if p.ndim == 1:
+        p = p[None, :]
+    f, j = np.nonzero(p >= threshold)
+    return f, j, p[f, j]
+
+
+def derivative(s, h) -> np.ndarray:
+    """Derivative of the convolved output along j, d[F][Ns-M+1] (complex128):
+    central differences inside, one-sided at both ends (Ns - M + 1 >= 2)."""
+    s, h, F, M, squeeze = _bank(s, h)
+    d = np.empty((F, s.shape[0] - M + 1), dtype=np.complex128)
+    if _load().ols_oracle_derivative(s.shape[0], _ptr(s), M, F, _ptr(h), _ptr(d)) != 0:
+        raise ValueError("ols_oracle_derivative rejected the sizes (needs Ns - M + 1 >= 2)")
+    return d[0] if squeeze else d
+
+
+def derivative_at(s, h, f_idx, j_idx) -> np.ndarray:
+    """d_{f_idx[i]}[j_idx[i]] for each i (complex128)."""
+    s, h, F, M, _ = _bank(s, h)
+    fi = np.ascontiguousarray(f_idx, dtype=np.int64)
+    ji = np.ascontiguousarray(j_idx, dtype=np.int64)
+    if fi.shape != ji.shape:
+        raise ValueError("index arrays differ in shape")
+    out = np.empty(fi.shape, dtype=np.complex128)
+    if _load().ols_oracle_derivative_at(s.shape[0], _ptr(s), M, F, _ptr(h), fi.size, _ptr(fi), _ptr(ji),
+                                        _ptr(out)) != 0:
+        raise ValueError("ols_oracle_derivative_at rejected the sizes or an index")
     return out
 
 

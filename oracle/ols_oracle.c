@@ -218,3 +218,83 @@ int ols_oracle_conv_real_at(int64_t Ns, const float *s, int32_t M, int32_t F,
         out[i] = conv_one_real(s, M, h + (size_t)fi[i] * M, ji[i]);
     return 0;
 }
+
+/*
+ * Post-processing of the convolved output (Sec. 3.2's optional
+ * post-processing step; Sec. 4.3: per-element post-processing such as the
+ * power spectrum, and non-local post-processing such as the numerical
+ * derivative of the convolved signal, whose formula the paper does not give).
+ * Reading taken for the derivative: the central difference with one-sided
+ * differences at the two ends of each output stream,
+ *     d_f[j] = (y_f[j+1] - y_f[j-1]) / 2        0 < j < Nout-1
+ *     d_f[0] = y_f[1] - y_f[0],   d_f[Nout-1] = y_f[Nout-1] - y_f[Nout-2],
+ * defined for Nout >= 2.  The power is p_f[j] = |y_f[j]|^2.  Both are
+ * computed here from the FP64 outputs of conv_one.
+ */
+
+/* Derivative of filter f's output at j (Nout >= 2). */
+static void deriv_one(const float *s, int32_t M, const float *hf, int64_t Nout, int64_t j,
+                      double *out_re, double *out_im)
+{
+    const int64_t lo = (j == 0) ? j : j - 1;
+    const int64_t hi = (j == Nout - 1) ? j : j + 1;
+    const double scale = (hi - lo == 2) ? 0.5 : 1.0;
+    double ar, ai, br, bi;
+    conv_one(s, M, hf, lo, &ar, &ai);
+    conv_one(s, M, hf, hi, &br, &bi);
+    *out_re = (br - ar) * scale;
+    *out_im = (bi - ai) * scale;
+}
+
+/*
+ * p: [F][Ns-M+1] real (FP64) power of every output.  Returns 0, or -1 on
+ * invalid sizes.
+ */
+int ols_oracle_power(int64_t Ns, const float *s, int32_t M, int32_t F, const float *h, double *p)
+{
+    if (M < 1 || F < 1 || Ns < M) return -1;
+    const int64_t Nout = Ns - M + 1;
+    const int64_t total = (int64_t)F * Nout;
+    int64_t idx;
+#pragma omp parallel for schedule(static)
+    for (idx = 0; idx < total; ++idx) {
+        const int64_t f = idx / Nout, j = idx % Nout;
+        double yr, yi;
+        conv_one(s, M, h + 2 * (size_t)f * M, j, &yr, &yi);
+        p[idx] = yr * yr + yi * yi;
+    }
+    return 0;
+}
+
+/*
+ * d: [F][Ns-M+1] complex (FP64) derivative of every output stream.  Returns
+ * 0, or -1 on invalid sizes (including Nout < 2).
+ */
+int ols_oracle_derivative(int64_t Ns, const float *s, int32_t M, int32_t F, const float *h, double *d)
+{
+    if (M < 1 || F < 1 || Ns < M + 1) return -1;
+    const int64_t Nout = Ns - M + 1;
+    const int64_t total = (int64_t)F * Nout;
+    int64_t idx;
+#pragma omp parallel for schedule(static)
+    for (idx = 0; idx < total; ++idx) {
+        const int64_t f = idx / Nout, j = idx % Nout;
+        deriv_one(s, M, h + 2 * (size_t)f * M, Nout, j, &d[2 * idx], &d[2 * idx + 1]);
+    }
+    return 0;
+}
+
+/* Selected derivatives: out[i] = d_{fi[i]}[ji[i]].  Returns 0, or -1. */
+int ols_oracle_derivative_at(int64_t Ns, const float *s, int32_t M, int32_t F, const float *h, int64_t n,
+                             const int64_t *fi, const int64_t *ji, double *out)
+{
+    if (M < 1 || F < 1 || Ns < M + 1) return -1;
+    const int64_t Nout = Ns - M + 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (fi[i] < 0 || fi[i] >= F || ji[i] < 0 || ji[i] >= Nout) return -1;
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i)
+        deriv_one(s, M, h + 2 * (size_t)fi[i] * M, Nout, ji[i], &out[2 * i], &out[2 * i + 1]);
+    return 0;
+}

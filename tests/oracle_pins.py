@@ -309,3 +309,76 @@ def pin_real_is_complex_on_real_data(conv_real, conv, seed=24):
 
 
 REAL_QUICK_PINS = (pin_real_bruteforce, pin_real_delta_shift, pin_real_closed_forms)
+
+
+# ------------------------------------------------- post-processing of the output
+# Sec. 4.3: per-element post-processing (the power spectrum) and non-local
+# post-processing (the numerical derivative of the convolved signal; the
+# paper gives no formula, the reading is the central difference with
+# one-sided ends).  Each pin takes (power, derivative, conv).
+
+def pin_derivative_is_numpy_gradient(power, derivative, conv, seed=31):
+    """numpy.gradient with unit spacing is the same difference scheme (central
+    inside, first-order one-sided at both ends); it is an independent
+    implementation of the reading."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    for (Ns, M, F) in ((2, 1, 1), (3, 2, 2), (40, 7, 3), (300, 33, 2)):
+        s = (g.uniform(-1, 1, Ns) + 1j * g.uniform(-1, 1, Ns)).astype(np.complex64)
+        h = (g.normal(size=(F, M)) + 1j * g.normal(size=(F, M))).astype(np.complex64)
+        d = derivative(s, h)
+        ref = np.gradient(conv(s, h), axis=1)
+        assert d.shape == ref.shape
+        assert np.max(np.abs(d - ref)) <= 1e-13 * (np.max(np.abs(ref)) + 1.0), (Ns, M, F)
+
+
+def pin_derivative_ramp(power, derivative, conv):
+    """s[n] = n (exact in FP32) with a delta filter gives y[j] = j + M - 1 - d,
+    whose derivative is exactly 1 everywhere, ends included."""
+    Ns = 500
+    s = np.arange(Ns).astype(np.complex64)
+    for M in (1, 2, 17):
+        for dpos in sorted({0, M - 1}):
+            h = np.zeros(M, np.complex64)
+            h[dpos] = 1
+            assert np.array_equal(derivative(s, h), np.ones(Ns - M + 1, np.complex128)), (M, dpos)
+
+
+def pin_derivative_closed_form(power, derivative, conv, seed=32):
+    """s[n] = exp(i w n) gives y[j] = A exp(i w j), A = exp(i w (M-1)) sum_k h[k]
+    exp(-i w k); its derivative is y[j] i sin(w) inside, y[j] (exp(i w) - 1) at
+    j = 0 and y[j] (1 - exp(-i w)) at the last output.  The power is |A|^2."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    Ns, M, w = 400, 9, 0.3
+    n = np.arange(Ns)
+    s = np.exp(1j * w * n).astype(np.complex64)
+    h = (g.normal(size=M) + 1j * g.normal(size=M)).astype(np.complex64)
+    # FP32-rounded input: the closed form uses the rounded samples' exact phases only approximately,
+    # so compare at the rounding level of complex64 (~1e-7 relative)
+    k = np.arange(M)
+    A = np.exp(1j * w * (M - 1)) * np.sum(h.astype(np.complex128) * np.exp(-1j * w * k))
+    j = np.arange(Ns - M + 1)
+    y = A * np.exp(1j * w * j)
+    ref = y * 1j * np.sin(w)
+    ref[0] = y[0] * (np.exp(1j * w) - 1)
+    ref[-1] = y[-1] * (1 - np.exp(-1j * w))
+    d = derivative(s, h)
+    assert np.max(np.abs(d - ref)) <= 2e-6 * np.abs(A)
+    assert np.max(np.abs(power(s, h) - np.abs(A) ** 2)) <= 2e-6 * np.abs(A) ** 2
+
+
+def pin_power_is_squared_magnitude(power, derivative, conv, seed=33):
+    """p = |y|^2 = Re(y)^2 + Im(y)^2 of the same FP64 outputs, element by element."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    s = (g.uniform(-1, 1, 700) + 1j * g.uniform(-1, 1, 700)).astype(np.complex64)
+    h = (g.normal(size=(3, 21)) + 1j * g.normal(size=(3, 21))).astype(np.complex64)
+    y = conv(s, h)
+    assert np.array_equal(power(s, h), y.real * y.real + y.imag * y.imag)
+    # a delta filter returns |s|^2 of the shifted samples
+    e = np.zeros(5, np.complex64)
+    e[2] = 1
+    sd = s.astype(np.complex128)[2: 700 - 2]
+    assert np.array_equal(power(s, e), sd.real * sd.real + sd.imag * sd.imag)
+
+
+POST_PINS = (pin_derivative_is_numpy_gradient, pin_derivative_ramp, pin_derivative_closed_form,
+             pin_power_is_squared_magnitude)

@@ -208,3 +208,76 @@ def test_real_pins_catch_planted_mistake(name):
             except AssertionError:
                 caught.append(pin.__name__)
         assert caught, "planted mistake %s passed every real pin" % name
+
+
+@pytest.mark.parametrize("pin", P.POST_PINS)
+def test_oracle_post_pin(pin):
+    pin(oracle.power, oracle.derivative, oracle.conv)
+
+
+def test_oracle_post_sampled_and_detect():
+    g = np.random.Generator(np.random.PCG64(6))
+    s = (g.uniform(-1, 1, 800) + 1j * g.uniform(-1, 1, 800)).astype(np.complex64)
+    h = (g.normal(size=(3, 30)) + 1j * g.normal(size=(3, 30))).astype(np.complex64)
+    d = oracle.derivative(s, h)
+    fi = np.concatenate([g.integers(0, 3, 50), [0, 1, 2]])
+    ji = np.concatenate([g.integers(0, d.shape[1], 50), [0, d.shape[1] - 1, 1]])
+    assert np.array_equal(oracle.derivative_at(s, h, fi, ji), d[fi, ji])
+    p = oracle.power(s, h)
+    assert np.array_equal(oracle.power_at(s, h, fi, ji), p[fi, ji])
+    thr = float(np.quantile(p, 0.99))
+    f, j, pw = oracle.detect(s, h, thr)
+    assert f.size == int(np.sum(p >= thr)) and np.all(pw >= thr) and np.array_equal(pw, p[f, j])
+    with pytest.raises(ValueError):
+        oracle.derivative(s[:30], h)          # Nout = 1: no derivative
+
+
+POST_MUTANTS = {
+    "deriv_no_half": ("const double scale = (hi - lo == 2) ? 0.5 : 1.0;", "const double scale = 1.0;"),
+    "deriv_ends_halved": ("const double scale = (hi - lo == 2) ? 0.5 : 1.0;", "const double scale = 0.5;"),
+    "deriv_sign": ("*out_re = (br - ar) * scale;\n    *out_im = (bi - ai) * scale;",
+                   "*out_re = (ar - br) * scale;\n    *out_im = (ai - bi) * scale;"),
+    "deriv_backward_only": ("const int64_t hi = (j == Nout - 1) ? j : j + 1;", "const int64_t hi = j;"),
+    "power_minus": ("p[idx] = yr * yr + yi * yi;", "p[idx] = yr * yr - yi * yi;"),
+}
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(POST_MUTANTS))
+def test_post_pins_catch_planted_mistake(name):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "ols_oracle.c")).read()
+    old, new = POST_MUTANTS[name]
+    assert src.count(old) == 1, "mutation anchor not unique: " + name
+    with tempfile.TemporaryDirectory() as d:
+        cpath = os.path.join(d, "mut.c")
+        with open(cpath, "w") as fh:
+            fh.write(src.replace(old, new))
+        so = os.path.join(d, "libmut.so")
+        subprocess.run(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                        "-std=c11", "-o", so, cpath], check=True)
+        lib = ctypes.CDLL(so)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        for fn in ("ols_oracle_power", "ols_oracle_derivative", "ols_oracle_conv"):
+            getattr(lib, fn).argtypes = [i64, vp, i32, i32, vp, vp]
+
+        def call(fn, dtype):
+            def run(s, h):
+                s = np.ascontiguousarray(s, np.complex64)
+                h = np.ascontiguousarray(h, np.complex64)
+                sq = h.ndim == 1
+                h2 = h[None] if sq else h
+                F, M = h2.shape
+                out = np.empty((F, len(s) - M + 1), dtype)
+                assert getattr(lib, fn)(len(s), s.ctypes.data, M, F, h2.ctypes.data, out.ctypes.data) == 0
+                return out[0] if sq else out
+            return run
+
+        power, deriv, conv = (call("ols_oracle_power", np.float64), call("ols_oracle_derivative", np.complex128),
+                              call("ols_oracle_conv", np.complex128))
+        caught = []
+        for pin in P.POST_PINS:
+            try:
+                pin(power, deriv, conv)
+            except AssertionError:
+                caught.append(pin.__name__)
+        assert caught, "planted mistake %s passed every post-processing pin" % name
