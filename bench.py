@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ns", type=int, default=0, help="override the signal length (profiling a smaller case)")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads (batched, adjoint, tensor-core)")
-    ap.add_argument("--only", choices=["plain_1x1", "diff", "batched", "tensor_core", "r2r"], default=None,
+    ap.add_argument("--only", choices=["plain_1x1", "diff", "batched", "tensor_core", "r2r", "post"], default=None,
                     help="run just this other workload (with --ns: its signal length) and print its numbers")
     return ap.parse_args()
 
@@ -245,6 +245,8 @@ def measure_others(peak, only=None, ns=0):
         _tensor_core(res, samples, peak)
     if want("r2r"):
         _r2r(res, samples, peak)
+    if want("post"):
+        _post(res, samples, peak)
     torch.cuda.empty_cache()
     return res, samples
 
@@ -425,6 +427,57 @@ def _r2r(res, samples, peak):
     del y, s
 
 
+def _post(res, samples, peak):
+    """Post-processing fused into the convolution (Sec. 4.3) on the filter-bank
+    shape: power |y|^2, threshold detection, derivative of y."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1910_01972_gb300 import Plan
+    cfg = synth.PLAIN_BANK
+    s_np, h_np = synth.plain_inputs(cfg)
+    p = Plan(cfg.M, cfg.F, cfg.N)
+    p.set_filters(torch.from_numpy(h_np).cuda())
+    s = torch.from_numpy(s_np).cuda()
+    nout = cfg.Ns - cfg.M + 1
+    outs = cfg.F * nout
+    base = 8 * cfg.Ns + 8 * cfg.F * cfg.N
+    pw = p.convolve_power(s)
+    ms_p = _time_events(lambda: p.convolve_power(s, out=pw), 20)
+    g = np.random.Generator(np.random.PCG64(10))
+    fi = g.integers(0, cfg.F, 3000)
+    ji = g.integers(0, nout, 3000)
+    fit, jit = torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()
+    samples["post"] = {"s": s_np, "h": h_np, "fi": fi, "ji": ji, "p": pw[fit, jit].cpu().numpy()}
+    thr = float(torch.quantile(pw.flatten()[: 1 << 22], 0.9999).item())
+    del pw
+    cap = 1 << 20
+    rec, cnt = p.convolve_detect(s, thr, cap)
+    ms_d = _time_events(lambda: p.convolve_detect(s, thr, cap), 20)
+    torch.cuda.synchronize()
+    found = int(cnt.item())
+    del rec, cnt
+    d = p.convolve_derivative(s)
+    ms_v = _time_events(lambda: p.convolve_derivative(s, out=d), 20)
+    samples["post"]["d"] = d[fit, jit].cpu().numpy()
+    del d
+    b_p = base + 4 * outs
+    b_d = base + 16 * min(found, cap)
+    b_v = base + 8 * outs
+    res["post"] = {"workload": cfg.name,
+                   "power": {"value": outs / (ms_p * 1e-3), "unit": UNIT, "ms": ms_p,
+                             "hbm_frac": b_p / (ms_p * 1e-3) / 1e9 / peak, "algorithmic_bytes": b_p},
+                   "detect": {"value": outs / (ms_d * 1e-3), "unit": UNIT, "ms": ms_d, "threshold": thr,
+                              "candidates": found, "hbm_frac": b_d / (ms_d * 1e-3) / 1e9 / peak,
+                              "algorithmic_bytes": b_d},
+                   "derivative": {"value": outs / (ms_v * 1e-3), "unit": UNIT, "ms": ms_v,
+                                  "hbm_frac": b_v / (ms_v * 1e-3) / 1e9 / peak, "algorithmic_bytes": b_v,
+                                  "note": "segments advance by L-2 (1790 of 2048 points) so each output's "
+                                          "neighbours are in its own segment"}}
+    p.close()
+    del s
+
+
 def others_errors(samples):
     """Relative L2 errors of the other workloads' sampled outputs against the oracle."""
     import numpy as np
@@ -437,6 +490,13 @@ def others_errors(samples):
             num += float(np.sum(np.abs(got - ref) ** 2))
             den += float(np.sum(np.abs(ref) ** 2))
         out["batched"] = (num / den) ** 0.5
+    if samples.get("post"):
+        d = samples["post"]
+        ref_p = oracle.power_at(d["s"], d["h"], d["fi"], d["ji"])
+        out["post_power"] = float(np.linalg.norm(d["p"].astype(np.float64) - ref_p) / np.linalg.norm(ref_p))
+        ref_d = oracle.derivative_at(d["s"], d["h"], d["fi"], d["ji"])
+        ref_y = oracle.conv_at(d["s"], d["h"], d["fi"], d["ji"])
+        out["post_derivative_vs_y_norm"] = float(np.linalg.norm(d["d"] - ref_d) / np.linalg.norm(ref_y))
     if samples.get("r2r"):
         d = samples["r2r"]
         ref = oracle.conv_real_at(d["s"], d["h"], d["fi"], d["ji"])

@@ -190,6 +190,60 @@ OLS_API int ols_set_filters_real(ols_plan_t plan, const float *h, void *stream);
  */
 OLS_API int ols_convolve_real(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Post-processing fused into the convolution kernel (Sec. 3.2 lists an
+ * optional post-processing step after the discard; Sec. 4.3 distinguishes
+ * per-element post-processing such as the power spectrum from non-local
+ * post-processing such as the numerical derivative, which needs each
+ * output's neighbours; Sec. 4.4 notes that reducing the output, e.g. by
+ * candidate selection, is what keeps the device-to-host transfer small).
+ * FP32 complex plans (OLS_FLAG_FP32) only; each is one kernel launch and the
+ * convolved y itself is never written.
+ * --------------------------------------------------------------------- */
+
+/*
+ * Power of the convolved output: p[f][j] = |y_f[j]|^2 (FP32), y as in
+ * ols_convolve.  s: device [Ns] complex; p: device [F][Ns-M+1] float,
+ * 4-byte aligned.  Errors: INVALID (pointers, Ns < M), UNSUPPORTED (not an
+ * FP32 complex plan), NOT_READY, CUDA.
+ */
+OLS_API int ols_convolve_power(ols_plan_t plan, const float *s, int64_t Ns, float *p, void *stream);
+
+/* One detection: output index j of filter f whose power |y_f[j]|^2 reached
+ * the threshold. */
+typedef struct {
+    int64_t j;
+    int32_t f;
+    float power;
+} ols_candidate;
+
+/*
+ * Candidate selection on the power of the convolved output: every (f, j)
+ * with |y_f[j]|^2 >= threshold is appended to cand (device array of
+ * `capacity` records) in no particular order; *count (device, 8-byte
+ * aligned) receives the total number found, which may exceed capacity (the
+ * records beyond it are dropped).  The call zeroes *count itself (a memset
+ * on `stream`, before the kernel).  Errors: INVALID (pointers, Ns < M,
+ * capacity < 0), UNSUPPORTED (not an FP32 complex plan), NOT_READY, CUDA.
+ */
+OLS_API int ols_convolve_detect(ols_plan_t plan, const float *s, int64_t Ns, float threshold,
+                                ols_candidate *cand, int64_t capacity, unsigned long long *count,
+                                void *stream);
+
+/*
+ * Numerical derivative of the convolved output along j (the paper's
+ * non-local post-processing example, Sec. 4.3; the paper gives no formula,
+ * this is the central difference with one-sided ends):
+ *   d_f[j] = (y_f[j+1] - y_f[j-1]) / 2   for 0 < j < Nout-1,
+ *   d_f[0] = y_f[1] - y_f[0],   d_f[Nout-1] = y_f[Nout-1] - y_f[Nout-2].
+ * Each segment advances by L-2 outputs instead of L so that every derivative
+ * it writes has both neighbours among its own unaliased outputs.
+ * s: device [Ns] complex; d: device [F][Ns-M+1] complex.
+ * Errors: INVALID (pointers, Ns - M + 1 < 2), UNSUPPORTED (not an FP32
+ * complex plan, or N - M + 1 < 3), NOT_READY, CUDA.
+ */
+OLS_API int ols_convolve_derivative(ols_plan_t plan, const float *s, int64_t Ns, float *d, void *stream);
+
 /*
  * The same convolution with HOST buffers (what a user outside the device
  * calls, Sec. 4.4 discusses the PCI-e cost): s_host [Ns] complex, y_host

@@ -15,7 +15,8 @@ import torch
 from . import _native
 from ._native import OLSError, check
 
-__all__ = ["Plan", "BatchPlan", "OLSError", "geometry", "spectrum_order", "convolve", "ols_conv", "autotune"]
+__all__ = ["Plan", "BatchPlan", "OLSError", "geometry", "spectrum_order", "convolve", "ols_conv", "autotune",
+           "decode_candidates"]
 
 
 def _stream_ptr(device) -> int:
@@ -127,6 +128,52 @@ class Plan:
               "ols_convolve")
         return out
 
+    def _signal(self, s: torch.Tensor) -> int:
+        _require(s, "s", self.device)
+        if s.dim() != 1:
+            raise ValueError("s must be 1-D")
+        if s.shape[0] < self.M:
+            raise ValueError("signal shorter than the filter (Ns < M)")
+        return s.shape[0] - self.M + 1
+
+    def convolve_power(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """|y|^2 fused into the convolution: s [Ns] -> p [F][Ns-M+1] float32."""
+        Nout = self._signal(s)
+        if out is None:
+            out = torch.empty((self.F, Nout), dtype=torch.float32, device=self.device)
+        _require_real(out, "out", self.device)
+        if tuple(out.shape) != (self.F, Nout):
+            raise ValueError("out must have shape [F][Ns-M+1]")
+        check(_native.ols_convolve_power(self._h, s.data_ptr(), s.shape[0], out.data_ptr(),
+                                         _stream_ptr(self.device)), "ols_convolve_power")
+        return out
+
+    def convolve_detect(self, s: torch.Tensor, threshold: float, capacity: int):
+        """Candidates (f, j) with |y_f[j]|^2 >= threshold.  Returns (records,
+        count): records is a device int64 tensor [capacity][2] holding the C
+        records (j; f and power packed in the second word, see
+        ``decode_candidates``), count a device uint64-as-int64 tensor [1]."""
+        self._signal(s)
+        rec = torch.empty((max(int(capacity), 1), 2), dtype=torch.int64, device=self.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        check(_native.ols_convolve_detect(self._h, s.data_ptr(), s.shape[0], float(threshold), rec.data_ptr(),
+                                          int(capacity), cnt.data_ptr(), _stream_ptr(self.device)),
+              "ols_convolve_detect")
+        return rec, cnt
+
+    def convolve_derivative(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Derivative of the convolved output along j (central differences,
+        one-sided at the ends): s [Ns] -> d [F][Ns-M+1] complex64."""
+        Nout = self._signal(s)
+        if out is None:
+            out = torch.empty((self.F, Nout), dtype=torch.complex64, device=self.device)
+        _require(out, "out", self.device)
+        if tuple(out.shape) != (self.F, Nout):
+            raise ValueError("out must have shape [F][Ns-M+1]")
+        check(_native.ols_convolve_derivative(self._h, s.data_ptr(), s.shape[0], out.data_ptr(),
+                                              _stream_ptr(self.device)), "ols_convolve_derivative")
+        return out
+
     def set_filters_real(self, h: torch.Tensor) -> None:
         """Real-to-real plans (flags=OLS_FLAG_R2R): h [F][M] float32 on the plan's device."""
         _require_real(h, "h", self.device)
@@ -212,6 +259,18 @@ class Plan:
         rc, v = _native.ols_plan_status(self._h, reset)
         check(rc, "ols_plan_status")
         return v
+
+
+def decode_candidates(records: torch.Tensor, count: int):
+    """(f, j, power) numpy arrays of the first min(count, capacity) records
+    written by ``Plan.convolve_detect`` (record layout of ols_candidate)."""
+    n = min(int(count), records.shape[0])
+    r = records[:n].cpu()
+    j = r[:, 0].numpy().copy()
+    w = r[:, 1].contiguous()
+    f = w.view(torch.int32).view(n, 2)[:, 0].numpy().copy()
+    p = w.view(torch.float32).view(n, 2)[:, 1].numpy().copy()
+    return f, j, p
 
 
 def autotune(M: int, F: int, model_only: bool = False) -> int:

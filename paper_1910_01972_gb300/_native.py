@@ -47,6 +47,9 @@ SIGNATURES = [
     ("ols_get_spectra", cint, [vp, vp, vp]),
     ("ols_convolve", cint, [vp, vp, i64, vp, vp]),
     ("ols_convolve_host", cint, [vp, vp, i64, vp, vp]),
+    ("ols_convolve_power", cint, [vp, vp, i64, vp, vp]),
+    ("ols_convolve_detect", cint, [vp, vp, i64, ctypes.c_float, vp, i64, vp, vp]),
+    ("ols_convolve_derivative", cint, [vp, vp, i64, vp, vp]),
     ("ols_set_filters_real", cint, [vp, vp, vp]),
     ("ols_convolve_real", cint, [vp, vp, i64, vp, vp]),
     ("ols_backward_workspace", cint, [vp, i64, cint, cint, ctypes.POINTER(ctypes.c_size_t)]),
@@ -144,6 +147,19 @@ def ols_get_spectra(plan, H_ptr: int, stream: int) -> int:
 
 def ols_convolve(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
     return lib().ols_convolve(plan, s_ptr, Ns, y_ptr, stream)
+
+
+def ols_convolve_power(plan, s_ptr: int, Ns: int, p_ptr: int, stream: int) -> int:
+    return lib().ols_convolve_power(plan, s_ptr, Ns, p_ptr, stream)
+
+
+def ols_convolve_detect(plan, s_ptr: int, Ns: int, threshold: float, cand_ptr, capacity: int, count_ptr: int,
+                        stream: int) -> int:
+    return lib().ols_convolve_detect(plan, s_ptr, Ns, threshold, cand_ptr, capacity, count_ptr, stream)
+
+
+def ols_convolve_derivative(plan, s_ptr: int, Ns: int, d_ptr: int, stream: int) -> int:
+    return lib().ols_convolve_derivative(plan, s_ptr, Ns, d_ptr, stream)
 
 
 def ols_set_filters_real(plan, h_ptr: int, stream: int) -> int:

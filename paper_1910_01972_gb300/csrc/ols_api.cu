@@ -113,6 +113,7 @@ static int log2_exact(int64_t N) {
 }
 
 static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
+static bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
 
 // The fused convolution in the plan's arithmetic (FP32 or tensor-core split).
 // The N = 2048 single-warp-per-segment kernel (64 points per thread, one
@@ -316,6 +317,7 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     }
     if (e == cudaSuccess) e = launch_tw64(p->tw64, (int)N, 0);
     if (e == cudaSuccess) e = prepare_forward(*p);
+    if (e == cudaSuccess && flags == OLS_FLAG_FP32) e = post_prepare(*p);
     if (e == cudaSuccess) e = prepare_backward(*p);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -387,8 +389,6 @@ int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *st
     return status_of(e);
 }
 
-static bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
-
 int ols_set_filters_real(ols_plan_t plan, const float *h, void *stream) {
     if (!plan || !h || !aligned4(h)) return OLS_ERR_INVALID;
     if (plan->flags != OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
@@ -410,6 +410,69 @@ int ols_convolve_real(ols_plan_t plan, const float *s, int64_t Ns, float *y, voi
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
     if (rc != OLS_OK) return rc;
     cudaError_t e = r2r_launch(*plan, s, Ns, y, L, nseg, Nout, (cudaStream_t)stream);
+    plan->last_launches = 1;
+    return status_of(e);
+}
+
+// Argument checks shared by the post-processing entry points.
+static int post_common(ols_plan_t plan, const float *s, int64_t Ns, PostArgs *a) {
+    if (!plan || !s || !aligned8(s)) return OLS_ERR_INVALID;
+    if (plan->flags != OLS_FLAG_FP32) return OLS_ERR_UNSUPPORTED;
+    if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    int64_t L, nseg, Nout;
+    int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
+    if (rc != OLS_OK) return rc;
+    *a = PostArgs{};
+    a->s = reinterpret_cast<const float2 *>(s);
+    a->Ns = Ns;
+    a->Nout = Nout;
+    a->step = L;
+    a->nseg = nseg;
+    return OLS_OK;
+}
+
+int ols_convolve_power(ols_plan_t plan, const float *s, int64_t Ns, float *p, void *stream) {
+    if (!p || !aligned4(p)) return OLS_ERR_INVALID;
+    PostArgs a;
+    int rc = post_common(plan, s, Ns, &a);
+    if (rc != OLS_OK) return rc;
+    a.mode = POST_POWER;
+    a.out = p;
+    cudaError_t e = post_launch(*plan, a, (cudaStream_t)stream);
+    plan->last_launches = 1;
+    return status_of(e);
+}
+
+int ols_convolve_detect(ols_plan_t plan, const float *s, int64_t Ns, float threshold, ols_candidate *cand,
+                        int64_t capacity, unsigned long long *count, void *stream) {
+    if (!count || ((uintptr_t)count & 7u) || capacity < 0 || (capacity > 0 && (!cand || !aligned8(cand))))
+        return OLS_ERR_INVALID;
+    PostArgs a;
+    int rc = post_common(plan, s, Ns, &a);
+    if (rc != OLS_OK) return rc;
+    a.mode = POST_DETECT;
+    a.thr = threshold;
+    a.cand = cand;
+    a.count = count;
+    a.cap = capacity;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = post_launch(*plan, a, (cudaStream_t)stream);
+    plan->last_launches = 1;
+    return status_of(e);
+}
+
+int ols_convolve_derivative(ols_plan_t plan, const float *s, int64_t Ns, float *d, void *stream) {
+    if (!d || !aligned8(d)) return OLS_ERR_INVALID;
+    PostArgs a;
+    int rc = post_common(plan, s, Ns, &a);
+    if (rc != OLS_OK) return rc;
+    if (a.Nout < 2) return OLS_ERR_INVALID;
+    if (a.step < 3) return OLS_ERR_UNSUPPORTED;     // each segment needs L - 2 >= 1 outputs
+    a.mode = POST_DERIV;
+    a.step -= 2;
+    a.nseg = (a.Nout + a.step - 1) / a.step;
+    a.out = d;
+    cudaError_t e = post_launch(*plan, a, (cudaStream_t)stream);
     plan->last_launches = 1;
     return status_of(e);
 }

@@ -70,6 +70,7 @@ struct ols_plan_s {
     // two-segments-per-thread kernel (N >= 2048)
     float4 *tw_pair = nullptr;   // twiddle table as broadcast pairs (wr, wr, wi, wi)
     int pair_grid_cap = 0;
+    int post_grid_cap[3] = {0, 0, 0};  // post-processing kernels (power, detect, derivative)
     // real-to-real plans (OLS_FLAG_R2R)
     float2 *hpack = nullptr;     // [ceil(F/2)][M] paired real filters h_{2p} + i h_{2p+1}
     int r2r_grid_cap = 0;
@@ -122,6 +123,21 @@ void spectral_order_w64(int32_t *nu);
 cudaError_t pair_prepare(ols_plan_s &p);
 cudaError_t pair_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
                         int64_t Nout, cudaStream_t st);
+
+// Fused OLS with post-processing of the output (ols_post.cu).
+enum PostMode { POST_POWER = 0, POST_DETECT = 1, POST_DERIV = 2 };
+struct PostArgs {
+    int mode;
+    const float2 *s;
+    int64_t Ns, Nout, step, nseg;   // step: outputs per segment (L, or L-2 for the derivative)
+    void *out;                      // POWER: float [F][Nout]; DERIV: float2 [F][Nout]
+    float thr;                      // DETECT
+    ols_candidate *cand;
+    unsigned long long *count;
+    int64_t cap;
+};
+cudaError_t post_prepare(ols_plan_s &p);
+cudaError_t post_launch(const ols_plan_s &p, const PostArgs &a, cudaStream_t st);
 
 // Real-to-real form (ols_r2r.cu): filters paired as h_{2p} + i h_{2p+1}.
 cudaError_t launch_pack_real_pairs(const float *h, int M, int F, float2 *g, cudaStream_t st);

@@ -1,0 +1,229 @@
+// ols_post.cu -- the fused OLS kernel with post-processing of the convolved
+// output inside the kernel, before anything is written (Sec. 3.2: OLS's
+// "optional post-processing" step; Sec. 4.3: per-element and non-local
+// post-processing; Sec. 4.4: reducing the output before it leaves the GPU).
+//
+// Three epilogues on the same segment body as ols_forward.cu (segment FFT
+// kept in registers for all filters; per filter the point-wise product, the
+// inverse FFT and the discard of aliased samples):
+// * POWER   (per element)   p_f[j] = |y_f[j]|^2, written as FP32 (half the
+//   output bytes of y);
+// * DETECT  (per element + selection) the candidates (f, j) whose power
+//   reaches a threshold, appended to a caller list through one atomic per
+//   warp and store step (warp-aggregated), nothing else written;
+// * DERIV   (non-local)     the numerical derivative of y along j: central
+//   differences (y[j+1] - y[j-1]) / 2 inside, one-sided differences at j = 0
+//   and j = Nout-1.  Each segment advances by L-2 instead of L and starts one
+//   output early, so every derivative it writes has both neighbours among
+//   its own unaliased samples (the "immediate neighbourhood" of Sec. 4.3);
+//   the neighbours are exchanged through a shared-memory buffer of their own.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ols_fft_passes.cuh"
+#include "ols_internal.h"
+
+namespace ols {
+
+template <int LOG2N, int MODE>
+struct PostGeo {
+    using G = Geo<LOG2N>;
+    static constexpr int BUFS = G::XBUFS + (MODE == POST_DERIV ? 1 : 0);
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)(G::SEGS * BUFS * G::PADN);
+    // the derivative's epilogue holds more live values: one resident block
+    // fewer per SM keeps it free of register spills
+    static constexpr int MINB = (MODE == POST_DERIV && G::MINB > 1) ? G::MINB - 1 : G::MINB;
+};
+
+template <int LOG2N, int MODE>
+__global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, (PostGeo<LOG2N, MODE>::MINB))
+ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
+                const float2 *__restrict__ twg, void *__restrict__ out, int M, int F, long long step,
+                long long nseg, long long Nout, float thr, ols_candidate *__restrict__ cand,
+                unsigned long long *__restrict__ count, long long cap) {
+    using G = Geo<LOG2N>;
+    using PG = PostGeo<LOG2N, MODE>;
+    extern __shared__ float4 smem_raw[];
+    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+    const int slot = threadIdx.x / G::T;
+    const int t = threadIdx.x % G::T;
+    float2 *bufs = smem + slot * PG::BUFS * G::PADN;
+    float2 *dbuf = bufs + G::XBUFS * G::PADN;        // DERIV: the output's neighbourhood
+    const TwGlobal tw{twg};
+    // circular position of a segment's first output, and its input offset
+    const int n0 = MODE == POST_DERIV ? M : M - 1;
+    const long long off = MODE == POST_DERIV ? -1 : 0;
+    int xc = 0;
+    const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
+    for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const long long seg = blk * G::SEGS + slot;
+        const bool active = seg < nseg;
+        const long long j0 = seg * step;                 // first output of this segment
+        const long long start = j0 + off;                // first input sample (may be -1)
+
+        // segment load: samples start + k T + t inside [0, Ns), zero elsewhere
+        float2 X[16];
+        {
+            const long long avail = active ? (Ns - start) : 0;
+            const int lim = (int)(avail < G::N ? avail : G::N);
+            const int first = active ? (int)(-start > 0 ? -start : 0) : 0;   // 1 only before s[0]
+            const float2 *src = sig + (active ? start : 0) + t;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int n = k * G::T + t;
+                X[k] = (n >= first && n < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+            }
+        }
+        forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
+
+        const long long rem = active ? (Nout - j0) : 0;
+        const int span = (int)(rem < step ? rem : step);
+
+        float4 hn[8];
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
+        for (int f = 0; f < F; ++f) {
+            float2 x[16];
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) {
+                x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].y));
+                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
+            }
+            if (f + 1 < F) {
+                const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
+#pragma unroll
+                for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+            }
+            inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
+
+            if constexpr (MODE == POST_POWER) {
+                float *dst = static_cast<float *>(out) + (size_t)f * (size_t)Nout + (j0 - n0);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    if ((unsigned)(n - n0) < (unsigned)span) dst[n] = fmaf(x[k].x, x[k].x, x[k].y * x[k].y);
+                }
+            } else if constexpr (MODE == POST_DETECT) {
+                const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    const float p = fmaf(x[k].x, x[k].x, x[k].y * x[k].y);
+                    const bool hit = (unsigned)(n - n0) < (unsigned)span && p >= thr;
+                    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+                    if (mask) {
+                        unsigned long long base = 0;
+                        const unsigned leader = __ffs(mask) - 1;
+                        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        if (hit) {
+                            const unsigned long long i = base + __popc(mask & ((1u << lane) - 1u));
+                            if (i < (unsigned long long)cap) {
+                                ols_candidate c;
+                                c.j = j0 + (n - n0);
+                                c.f = f;
+                                c.power = p;
+                                cand[i] = c;
+                            }
+                        }
+                    }
+                }
+            } else {
+                // write y (circular order) to the neighbourhood buffer, padded q -> q + q/16
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    dbuf[n + (n >> 4)] = x[k];
+                }
+                __syncthreads();
+                float2 *dst = static_cast<float2 *>(out) + (size_t)f * (size_t)Nout + (j0 - n0);
+                // circular positions of outputs j = 0 and j = Nout-1 (one-sided ends), if in this segment
+                const int n_first = j0 == 0 ? n0 : -2;
+                const int n_last = (rem <= step) ? (int)(rem - 1) + n0 : -2;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    if ((unsigned)(n - n0) < (unsigned)span) {
+                        const int lo = (n == n_first) ? n : n - 1;
+                        const int hi = (n == n_last) ? n : n + 1;
+                        const float sc = (lo == n || hi == n) ? 1.f : 0.5f;
+                        const float2 a = dbuf[lo + (lo >> 4)], b = dbuf[hi + (hi >> 4)];
+                        dst[n] = make_float2((b.x - a.x) * sc, (b.y - a.y) * sc);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int LOG2N, int MODE>
+static cudaError_t post_prepare_nm(ols_plan_s &p) {
+    using G = Geo<LOG2N>;
+    using PG = PostGeo<LOG2N, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(ols_post_kernel<LOG2N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PG::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_post_kernel<LOG2N, MODE>, G::BLOCK, PG::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    p.post_grid_cap[MODE] = per_sm * p.sm_count;
+    return cudaSuccess;
+}
+
+template <int LOG2N>
+static cudaError_t post_prepare_n(ols_plan_s &p) {
+    cudaError_t e = post_prepare_nm<LOG2N, POST_POWER>(p);
+    if (e == cudaSuccess) e = post_prepare_nm<LOG2N, POST_DETECT>(p);
+    if (e == cudaSuccess) e = post_prepare_nm<LOG2N, POST_DERIV>(p);
+    return e;
+}
+
+cudaError_t post_prepare(ols_plan_s &p) {
+    switch (p.log2N) {
+        case 8: return post_prepare_n<8>(p);
+        case 9: return post_prepare_n<9>(p);
+        case 10: return post_prepare_n<10>(p);
+        case 11: return post_prepare_n<11>(p);
+        case 12: return post_prepare_n<12>(p);
+        case 13: return post_prepare_n<13>(p);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LOG2N, int MODE>
+static cudaError_t post_launch_nm(const ols_plan_s &p, const PostArgs &a, cudaStream_t st) {
+    using G = Geo<LOG2N>;
+    using PG = PostGeo<LOG2N, MODE>;
+    const int64_t nblk = (a.nseg + G::SEGS - 1) / G::SEGS;
+    const int cap = p.post_grid_cap[MODE];
+    const int grid = (int)(nblk < cap ? nblk : cap);
+    ols_post_kernel<LOG2N, MODE><<<grid, G::BLOCK, PG::SMEM, st>>>(
+        a.s, a.Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, a.out, p.M, p.F, a.step, a.nseg, a.Nout, a.thr,
+        a.cand, a.count, a.cap);
+    return cudaGetLastError();
+}
+
+template <int LOG2N>
+static cudaError_t post_launch_n(const ols_plan_s &p, const PostArgs &a, cudaStream_t st) {
+    switch (a.mode) {
+        case POST_POWER: return post_launch_nm<LOG2N, POST_POWER>(p, a, st);
+        case POST_DETECT: return post_launch_nm<LOG2N, POST_DETECT>(p, a, st);
+        case POST_DERIV: return post_launch_nm<LOG2N, POST_DERIV>(p, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t post_launch(const ols_plan_s &p, const PostArgs &a, cudaStream_t st) {
+    switch (p.log2N) {
+        case 8: return post_launch_n<8>(p, a, st);
+        case 9: return post_launch_n<9>(p, a, st);
+        case 10: return post_launch_n<10>(p, a, st);
+        case 11: return post_launch_n<11>(p, a, st);
+        case 12: return post_launch_n<12>(p, a, st);
+        case 13: return post_launch_n<13>(p, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ols
