@@ -7,6 +7,12 @@ M-1 sample halo) with no communication.  The adjoint needs two reductions:
 dh is a sum over ranks, and the input gradient of rank r's slice overlaps the
 next rank's by M-1 samples, which one point-to-point exchange adds.
 
+The second way to split is along the filter bank: rank r convolves the whole
+signal with its own contiguous block of filters, so its outputs are whole
+rows of y and the forward pass needs no communication at all; in the adjoint
+each rank's dh rows are final and the input gradient ds is a sum over ranks
+(one all-reduce of Ns samples).
+
 Collectives use torch.distributed (gloo on CPU tensors, NCCL on CUDA tensors);
 the convolution itself is the caller's (the library's kernels on a GPU).
 """
@@ -64,5 +70,21 @@ def reduce_filter_gradient(dh: torch.Tensor, group=None) -> torch.Tensor:
     """Sum of the ranks' filter gradients (all ranks receive it)."""
     import torch.distributed as dist
     out = dh.clone()
+    dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
+    return out
+
+
+def filter_range(F: int, world: int, rank: int):
+    """[f0, f1) of the filters (rows of y, dh) owned by `rank` when the bank is
+    split across ranks (contiguous, sizes differ by at most one; a rank may
+    own none when F < world)."""
+    return output_range(F, world, rank)
+
+
+def reduce_signal_gradient(ds: torch.Tensor, group=None) -> torch.Tensor:
+    """Filter-split adjoint: the input gradient is the sum of every rank's
+    contribution (all ranks receive it)."""
+    import torch.distributed as dist
+    out = ds.clone()
     dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
     return out

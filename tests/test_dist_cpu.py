@@ -83,3 +83,68 @@ def test_two_rank_split_equals_whole_signal(world):
     same_y, e_ds, e_dh = q.get(timeout=5)
     assert same_y                      # each output is the same sequential sum: identical
     assert e_ds < 1e-12 and e_dh < 1e-12
+
+
+def _filter_worker(rank, world, port, Ns, M, F, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    import oracle
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g = np.random.Generator(np.random.PCG64(43))
+        s = (g.uniform(-1, 1, Ns) + 1j * g.uniform(-1, 1, Ns)).astype(np.complex64)
+        h = (g.normal(size=(F, M)) + 1j * g.normal(size=(F, M))).astype(np.complex64)
+        gy = g.normal(size=(F, Ns - M + 1)) + 1j * g.normal(size=(F, Ns - M + 1))
+        f0, f1 = parallel.filter_range(F, world, rank)
+        # forward: whole signal, own filters, no communication
+        y_loc = oracle.conv(s, h[f0:f1]) if f1 > f0 else np.zeros((0, Ns - M + 1), np.complex128)
+        parts = [None] * world
+        dist.all_gather_object(parts, (f0, y_loc))
+        # adjoint: own dh rows are final, ds is summed over ranks
+        if f1 > f0:
+            ds_loc, dh_loc = oracle.adjoint(s, h[f0:f1], gy[f0:f1])
+        else:
+            ds_loc, dh_loc = np.zeros(Ns, np.complex128), np.zeros((0, M), np.complex128)
+        ds_all = parallel.reduce_signal_gradient(torch.from_numpy(ds_loc)).numpy()
+        dh_parts = [None] * world
+        dist.all_gather_object(dh_parts, (f0, dh_loc))
+        if rank == 0:
+            y = np.concatenate([p[1] for p in sorted(parts, key=lambda p: p[0])], axis=0)
+            dh = np.concatenate([p[1] for p in sorted(dh_parts, key=lambda p: p[0])], axis=0)
+            ds_ref, dh_ref = oracle.adjoint(s, h, gy)
+            q.put((bool(np.array_equal(y, oracle.conv(s, h))), bool(np.array_equal(dh, dh_ref)),
+                   float(np.max(np.abs(ds_all - ds_ref)) / np.max(np.abs(ds_ref)))))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("F", [5, 1])
+def test_two_rank_filter_split_equals_whole_bank(F):
+    """The filter-bank split (no forward communication; ds summed over ranks)
+    reproduces the unsplit result; F = 1 leaves one rank without filters."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    Ns, M = 1500, 33
+    procs = [ctx.Process(target=_filter_worker, args=(r, world, port, Ns, M, F, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    for p in procs:
+        assert p.exitcode == 0, "rank failed"
+    same_y, same_dh, e_ds = q.get(timeout=5)
+    assert same_y and same_dh
+    assert e_ds < 1e-12
+
+
+@pytest.mark.parametrize("F,world", [(32, 4), (5, 2), (1, 2), (7, 7), (3, 8)])
+def test_filter_ranges_tile_the_bank(F, world):
+    seen = np.zeros(F, int)
+    for r in range(world):
+        f0, f1 = parallel.filter_range(F, world, r)
+        assert 0 <= f0 <= f1 <= F
+        seen[f0:f1] += 1
+    assert np.all(seen == 1)
