@@ -31,8 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "output samples/s (F*(Ns-M+1))"
 UNIT = "samples/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1910_01972_gb300/csrc/ols_forward.cu", "paper_1910_01972_gb300/csrc/ols_fft_passes.cuh",
-                  "paper_1910_01972_gb300/csrc/fft_regs.cuh"]
+KERNEL_SOURCES = ["paper_1910_01972_gb300/csrc/ols_forward.cu", "paper_1910_01972_gb300/csrc/ols_segment.cuh",
+                  "paper_1910_01972_gb300/csrc/ols_fft_passes.cuh", "paper_1910_01972_gb300/csrc/fft_regs.cuh",
+                  "paper_1910_01972_gb300/csrc/tmem.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_forward_bank_Ns8388608_F32_M257_N2048.md")
 
 
