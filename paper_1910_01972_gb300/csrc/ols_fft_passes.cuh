@@ -39,6 +39,9 @@
 #ifndef OLS_FWD_TW_TMEM
 #define OLS_FWD_TW_TMEM 0    // 1: fused kernels keep twiddles and the segment spectrum in TMEM
 #endif
+#ifndef OLS_FWD_X_TMEM
+#define OLS_FWD_X_TMEM 0     // 1: the forward kernel keeps only the segment spectrum in TMEM
+#endif
 #ifndef OLS_WARPS_PER_SM
 #define OLS_WARPS_PER_SM 16  // resident warps per SM the register budget must allow
 #endif
@@ -69,6 +72,8 @@ struct Geo {
     // TMEM twiddles: 128 columns per 128 threads (a thread's lane, 32 columns per pass)
     static constexpr uint32_t TMEM_COLS = (uint32_t)(BLOCK / 128) * 128u;
     static constexpr int TMEM_MAX_CTAS = 512 / (int)TMEM_COLS;
+    // segment spectrum alone in TMEM: 32 columns per 128 threads, rounded to the 32-column minimum
+    static constexpr uint32_t XT_COLS = (BLOCK / 128) * 32u < 32u ? 32u : (uint32_t)(BLOCK / 128) * 32u;
     // shared memory requested with TMEM twiddles: enough that no more CTAs fit on
     // an SM (228 KB) than TMEM can serve, so allocation never waits
     static constexpr size_t SMEM_TMEM = !OLS_FWD_TW_TMEM ? SMEM

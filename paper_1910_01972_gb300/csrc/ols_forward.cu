@@ -58,15 +58,36 @@ ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *_
     const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
     tw_tmem_fill<LOG2N>(twg, tw.base, t);
 #else
-    (void)tbase;
     const TwGlobal tw{twg};
+#if OLS_FWD_X_TMEM
+    // the segment spectrum in TMEM: 32 columns per 128 threads (a thread's lane)
+    if (threadIdx.x < 32) tmem::alloc(&tbase, G::XT_COLS);
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    const uint32_t xcol_t = tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 32u;
+#else
+    (void)tbase;
+    const uint32_t xcol_t = 0;
+#endif
 #endif
     int xc = 0;
     const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
     for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
         const long long seg = blk * G::SEGS + slot;
+#if OLS_FWD_TW_TMEM
         ols_segment<LOG2N>(sig, Ns, Hk, tw, y, M, F, L, Nout, seg, seg < nseg, bufs, t, xc);
+#else
+        ols_segment<LOG2N, TwGlobal, OLS_FWD_X_TMEM != 0>(sig, Ns, Hk, tw, y, M, F, L, Nout, seg, seg < nseg, bufs,
+                                                          t, xc, xcol_t);
+#endif
     }
+#if OLS_FWD_X_TMEM && !OLS_FWD_TW_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, G::XT_COLS);
+#endif
 #if OLS_FWD_TW_TMEM
     tmem::fence_before_sync();
     __syncthreads();

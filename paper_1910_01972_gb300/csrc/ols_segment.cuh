@@ -13,12 +13,14 @@
 
 namespace ols {
 
-template <int LOG2N, class TW>
+// XT: the segment spectrum waits in the thread's TMEM lane at column xcol_t
+// (32 columns) instead of registers; implied by TMEM twiddles (columns 96..127).
+template <int LOG2N, class TW, bool XT = std::is_same<TW, TwTmem>::value>
 __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long long Ns,
                                             const float4 *__restrict__ Hk, const TW &tw,
                                             float2 *__restrict__ y, int M, int F, long long L,
                                             long long Nout, long long seg, bool active, float2 *bufs,
-                                            int t, int &xc) {
+                                            int t, int &xc, uint32_t xcol_t = 0) {
     using G = Geo<LOG2N>;
     const int lo = M - 1;                      // aliased samples per segment
     const long long start = seg * L;
@@ -34,10 +36,11 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
             X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
     }
     forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
-    constexpr bool x_in_tmem = std::is_same<TW, TwTmem>::value;
+    constexpr bool x_in_tmem = XT;
     uint32_t xcol = 0;
     if constexpr (x_in_tmem) {
-        xcol = tw.base + 96;
+        if constexpr (std::is_same<TW, TwTmem>::value) xcol = tw.base + 96;
+        else xcol = xcol_t;
         tmem::st32(xcol, reinterpret_cast<const float *>(X));
         tmem::wait_st();
     }
