@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ns", type=int, default=0, help="override the signal length (profiling a smaller case)")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads (batched, adjoint, tensor-core)")
-    ap.add_argument("--only", choices=["plain_1x1", "diff", "batched", "tensor_core", "r2r", "post"], default=None,
+    ap.add_argument("--only", choices=["plain_1x1", "diff", "batched", "tensor_core", "r2r", "post", "cufft"], default=None,
                     help="run just this other workload (with --ns: its signal length) and print its numbers")
     return ap.parse_args()
 
@@ -248,6 +248,8 @@ def measure_others(peak, only=None, ns=0):
         _r2r(res, samples, peak)
     if want("post"):
         _post(res, samples, peak)
+    if want("cufft"):
+        _cufft_ols(res, samples, peak)
     torch.cuda.empty_cache()
     return res, samples
 
@@ -479,6 +481,49 @@ def _post(res, samples, peak):
     del s
 
 
+def _cufft_ols(res, samples, peak):
+    """Library comparison, not the product path: the unfused overlap-and-save of
+    Sec. 3.2 with cuFFT through torch.fft (segment separation, batched forward
+    FFT, product with every filter's spectrum, batched inverse FFT, discard of
+    the M-1 aliased samples), each step a separate kernel with its result in
+    HBM.  The paper's cuFFT-OLS uses load/store callbacks for the product and
+    the discard; torch.fft has none, so this is the callback-free form."""
+    import numpy as np
+    import torch
+    import synth
+    cfg = synth.PLAIN_BANK
+    s_np, h_np = synth.plain_inputs(cfg)
+    N, M, F = cfg.N, cfg.M, cfg.F
+    L = N - M + 1
+    nout = cfg.Ns - M + 1
+    nseg = (nout + L - 1) // L
+    s = torch.from_numpy(s_np).cuda()
+    H = torch.fft.fft(torch.from_numpy(h_np).cuda(), n=N, dim=1)                 # [F][N]
+    s_pad = torch.zeros((nseg - 1) * L + N, dtype=torch.complex64, device="cuda")
+    y = torch.empty((F, nseg * L), dtype=torch.complex64, device="cuda")
+
+    def step():
+        s_pad[: cfg.Ns].copy_(s)
+        seg = s_pad.unfold(0, N, L)                                               # [nseg][N] view
+        S = torch.fft.fft(seg, dim=1)                                             # forward FFTs
+        Yf = torch.fft.ifft(S[None, :, :] * H[:, None, :], dim=2)                 # [F][nseg][N]
+        y.view(F, nseg, L).copy_(Yf[:, :, M - 1:])                                # discard, merge
+    step()
+    ms = _time_events(step, 5)
+    torch.cuda.synchronize()
+    g = np.random.Generator(np.random.PCG64(11))
+    fi = g.integers(0, F, 3000)
+    ji = g.integers(0, nout, 3000)
+    samples["cufft"] = {"s": s_np, "h": h_np, "fi": fi, "ji": ji,
+                        "got": y[torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()].cpu().numpy()}
+    res["cufft_ols_comparison"] = {
+        "workload": cfg.name, "value": F * nout / (ms * 1e-3), "unit": UNIT, "ms": ms,
+        "note": "library comparison (not the product path): unfused overlap-and-save with cuFFT via torch.fft, "
+                "no callbacks; intermediate [F][nseg][N] complex in HBM"}
+    del y, s_pad, H, s
+    torch.cuda.empty_cache()
+
+
 def others_errors(samples):
     """Relative L2 errors of the other workloads' sampled outputs against the oracle."""
     import numpy as np
@@ -498,6 +543,10 @@ def others_errors(samples):
         ref_d = oracle.derivative_at(d["s"], d["h"], d["fi"], d["ji"])
         ref_y = oracle.conv_at(d["s"], d["h"], d["fi"], d["ji"])
         out["post_derivative_vs_y_norm"] = float(np.linalg.norm(d["d"] - ref_d) / np.linalg.norm(ref_y))
+    if samples.get("cufft"):
+        d = samples["cufft"]
+        ref = oracle.conv_at(d["s"], d["h"], d["fi"], d["ji"])
+        out["cufft_ols_comparison"] = float(np.linalg.norm(d["got"] - ref) / np.linalg.norm(ref))
     if samples.get("r2r"):
         d = samples["r2r"]
         ref = oracle.conv_real_at(d["s"], d["h"], d["fi"], d["ji"])
