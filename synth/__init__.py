@@ -162,3 +162,17 @@ def batch_inputs(spec: BatchSpec, index: int = 2):
     ss = [signal(g, n) for n in spec.Ns]
     hs = [filters(g, f, m) for f, m in zip(spec.F, spec.M)]
     return ss, hs
+
+
+def device_signal(Ns: int, seed: int, real: bool = False, device: str = "cuda"):
+    """A signal too large to draw on the host: re (and im) i.i.d. uniform[-1, 1]
+    drawn on the device by torch's seeded generator (Philox), complex64 (or
+    float32 when real).  Both sides read the same device values: tests gather
+    the windows they check and pass them to the oracle."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(SEED_BASE + int(seed))
+    n = Ns if real else 2 * Ns
+    x = torch.rand(n, generator=g, device=device, dtype=torch.float32)
+    x.mul_(2.0).sub_(1.0)
+    return x if real else x.view(torch.complex64)
