@@ -227,7 +227,7 @@ def measure_others(peak, only=None, ns=0):
     """Throughput of the other workloads on this GPU (outputs and samples for
     oracle checks are returned separately; the oracle runs in the CPU leg).
     `only` restricts the run to one workload (for profiling); `ns` then
-    overrides the differentiable workload's signal length."""
+    overrides the differentiable or real-to-real workload's signal length."""
     import torch
     res, samples = {}, {}
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")       # 256 MB > L2
@@ -245,7 +245,7 @@ def measure_others(peak, only=None, ns=0):
     if want("tensor_core"):
         _tensor_core(res, samples, peak)
     if want("r2r"):
-        _r2r(res, samples, peak)
+        _r2r(res, samples, peak, ns)
     if want("post"):
         _post(res, samples, peak)
     if want("cufft"):
@@ -402,13 +402,17 @@ def _tensor_core(res, samples, peak):
     del y, s, h
 
 
-def _r2r(res, samples, peak):
-    """Real-to-real form (Sec. 3.3's R2R variant) on the filter-bank shape."""
+def _r2r(res, samples, peak, ns=0):
+    """Real-to-real form (Sec. 3.3's R2R variant) on the filter-bank shape
+    (`ns` overrides the signal length)."""
+    import dataclasses
     import numpy as np
     import torch
     import synth
     from paper_1910_01972_gb300 import Plan, _native
     cfg = synth.R2R_BANK
+    if ns:
+        cfg = dataclasses.replace(cfg, Ns=ns, name=cfg.name.replace("Ns8388608", "Ns%d" % ns))
     s_np, h_np = synth.real_inputs(cfg)
     p = Plan(cfg.M, cfg.F, cfg.N, flags=_native.OLS_FLAG_R2R)
     p.set_filters_real(torch.from_numpy(h_np).cuda())

@@ -100,15 +100,23 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
                 for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
             }
             inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
-            float *dre = y + (size_t)(2 * p) * (size_t)Nout;
+            float *dre = y + (size_t)(2 * p) * (size_t)Nout + obase;
             float *dim = dre + Nout;
-            const bool has_im = 2 * p + 1 < F;
+            // the pair test is uniform: taken once per filter pair, so each
+            // store below is a plain predicated store
+            if (2 * p + 1 < F) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int n = k * G::T + t;
-                if ((unsigned)(n - lo) < (unsigned)span) {
-                    dre[obase + n] = x[k].x;
-                    if (has_im) dim[obase + n] = x[k].y;
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    const bool ok = (unsigned)(n - lo) < (unsigned)span;
+                    if (ok) dre[n] = x[k].x;
+                    if (ok) dim[n] = x[k].y;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    if ((unsigned)(n - lo) < (unsigned)span) dre[n] = x[k].x;
                 }
             }
         }
