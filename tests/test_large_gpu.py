@@ -85,3 +85,48 @@ def test_real_signal_beyond_2_to_31():
     plan.close()
     del y, s
     torch.cuda.empty_cache()
+
+
+def test_power_and_derivative_beyond_2_to_31():
+    """The post-processing kernels at the same size: |y|^2 and the derivative
+    (segments advancing by L-2 from an input offset of -1) past index 2^31."""
+    M, F, N = 64, 1, 512
+    g = np.random.Generator(np.random.PCG64(79))
+    h = synth.filters(g, F, M)
+    s = synth.device_signal(NS, seed=503)
+    plan = Plan(M, F, N)
+    plan.set_filters(torch.from_numpy(h).cuda())
+    q = plan.query(NS)
+    Nout, L = q["Nout"], q["L"]
+    j = _sample_outputs(Nout, L, 7)
+    jd = np.unique(np.clip(np.concatenate([j, _sample_outputs(Nout, L - 2, 8)]), 0, Nout - 1))
+    jt = torch.from_numpy(j).cuda()
+    p = plan.convolve_power(s)
+    got_p = p[0, jt].cpu().numpy().astype(np.float64)
+    del p
+    win = _windows(s, j, M)
+    ref_p = np.array([oracle.power_at(win[i], h, [0], [0])[0] for i in range(len(j))])
+    assert np.linalg.norm(got_p - ref_p) / np.linalg.norm(ref_p) <= 4e-6
+    d = plan.convolve_derivative(s)
+    got_d = d[0, torch.from_numpy(jd).cuda()].cpu().numpy()
+    del d
+    # the oracle's derivative on each output's local window: inputs for outputs
+    # j-1 .. j+1 (3 outputs, the middle one interior), or for the two outputs at
+    # an end of the stream (where the one-sided rule applies)
+    ref_d, ref_y = [], []
+    for jj in jd:
+        if jj == 0:
+            w0, k = 0, 0
+        elif jj == Nout - 1:
+            w0, k = jj - 1, 1
+        else:
+            w0, k = jj - 1, 1
+        n_loc = 2 if jj in (0, Nout - 1) else 3
+        w = _windows(s, np.array([w0]), M - 1 + n_loc)[0]
+        ref_d.append(oracle.derivative_at(w, h, [0], [k])[0])
+        ref_y.append(oracle.conv_at(w, h, [0], [k])[0])
+    ref_d, ref_y = np.array(ref_d), np.array(ref_y)
+    assert np.linalg.norm(got_d - ref_d) / np.linalg.norm(ref_y) <= TOL
+    plan.close()
+    del s
+    torch.cuda.empty_cache()
