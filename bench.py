@@ -335,6 +335,13 @@ def _batched(res, samples, peak):
     torch.cuda.synchronize()
     outs = sum(f * n for f, n in zip(spec.F, bp.Nout))
     ms_g = _time_events(graph.replay, 5)
+    # the same batch as one persistent launch per segment length
+    bq = BatchPlan(spec.Ns, spec.M, spec.F, N=bp.N, per_n=True)
+    bq.set_filters([torch.from_numpy(h).cuda() for h in hs])
+    bq.launch(st_t, yt_t)
+    ms_n = _time_events(lambda: bq.launch(st_t, yt_t), 5)
+    n_launches = bq.ngroups
+    bq.close()
     plans = []
     for b in range(bp.B):
         q = Plan(spec.M[b], spec.F[b], bp.N[b])
@@ -351,6 +358,8 @@ def _batched(res, samples, peak):
     res["batched"] = {"workload": "batch_B64_Ns2^16..2^22_F8..128_M33..1025_autotuned",
                       "value": outs / (ms_g * 1e-3), "unit": UNIT, "ms": ms_g, "hbm_frac": bb / (ms_g * 1e-3) / 1e9 / peak,
                       "launches": bp.ngroups, "segment_lengths": sorted(set(bp.N)),
+                      "per_segment_length": {"value": outs / (ms_n * 1e-3), "ms": ms_n, "launches": n_launches,
+                                             "note": "one persistent launch per distinct N, no graph"},
                       "per_signal": {"value": outs / (ms_p * 1e-3), "ms": ms_p, "launches": bp.B},
                       "speedup_vs_per_signal": ms_p / ms_g, "total_outputs": outs}
     graph.replay()

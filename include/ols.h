@@ -298,6 +298,9 @@ OLS_API int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, c
 
 /* Autotuner flag: use the cost model (N/L)(log2 N + c) instead of timing. */
 #define OLS_TUNE_MODEL (1u << 8)
+/* Batch flag: one persistent launch per distinct segment length instead of
+ * one launch for the whole batch. */
+#define OLS_BATCH_PER_N (1u << 9)
 
 /*
  * Pick the segment length N in {256, ..., 8192} (N >= M) for M taps and F
@@ -315,9 +318,12 @@ OLS_API int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N);
  * A batch of B independent problems of uneven size: signal b has Ns[b]
  * samples, F[b] filters of M[b] taps, segment length N[b] (N == NULL or
  * N[b] == 0: ols_autotune(M[b], F[b], flags)).  Host arrays of B entries.
- * Problems sharing a segment length form one persistent launch whose
- * resident blocks pull (problem, segment tile) work items from an atomic
- * ticket, most filters first; every segment is computed exactly as by
+ * The whole batch is ONE persistent launch: its resident blocks (512
+ * threads) pull (problem, segment tile) work items from an atomic ticket,
+ * the most expensive (F log2 N) first; a tile is 8192/N segments of one
+ * problem, each on a slot of N/16 threads with barriers of its own.  With
+ * OLS_BATCH_PER_N in flags, problems sharing a segment length form one
+ * persistent launch each instead.  Every segment is computed exactly as by
  * ols_convolve on the same N, so results are identical to per-problem calls.
  * Allocates per-problem spectra and the work tables.
  * Errors: INVALID (B < 1, NULL arrays, an Ns < M, M < 1, F < 1), UNSUPPORTED,
@@ -328,7 +334,8 @@ OLS_API int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const
 OLS_API int ols_batch_destroy(ols_batch_t batch);
 
 /* Segment length and output length of problem b, and the number of
- * persistent launches (distinct segment lengths) per call.  Any output
+ * persistent launches per call (1, or the distinct segment lengths with
+ * OLS_BATCH_PER_N).  Any output
  * pointer may be NULL.  Errors: INVALID. */
 OLS_API int ols_batch_query(ols_batch_t batch, int32_t b, int64_t *N, int64_t *Nout, int32_t *ngroups);
 
@@ -340,8 +347,9 @@ OLS_API int ols_batch_set_filters(ols_batch_t batch, const float *const *h, void
  * Convolve every problem: s_ptrs and y_ptrs are DEVICE arrays of B device
  * pointers (s_ptrs[b] -> [Ns[b]] complex, y_ptrs[b] -> [F[b]][Ns[b]-M[b]+1]
  * complex), read by the kernels, so the call enqueues only a memset of the
- * tickets and one launch per segment length: it can be captured in a CUDA
- * graph and replayed with new data behind the same pointers.
+ * ticket(s) and the launch (one, or one per segment length with
+ * OLS_BATCH_PER_N): it can be captured in a CUDA graph and replayed with new
+ * data behind the same pointers.
  * Errors: INVALID, NOT_READY, CUDA.
  */
 OLS_API int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_ptrs, void *stream);

@@ -283,12 +283,12 @@ def autotune(M: int, F: int, model_only: bool = False) -> int:
 
 class BatchPlan:
     """B independent problems of uneven size (Ns[b], M[b], F[b], N[b]; N None
-    or 0 entries are autotuned), convolved by one persistent launch per
-    distinct segment length."""
+    or 0 entries are autotuned), convolved by one persistent launch (or, with
+    per_n, one persistent launch per distinct segment length)."""
 
-    def __init__(self, Ns, M, F, N=None, model_only: bool = False):
-        rc, handle = _native.ols_batch_plan(list(Ns), list(M), list(F), None if N is None else list(N),
-                                            _native.OLS_TUNE_MODEL if model_only else 0)
+    def __init__(self, Ns, M, F, N=None, model_only: bool = False, per_n: bool = False):
+        flags = (_native.OLS_TUNE_MODEL if model_only else 0) | (_native.OLS_BATCH_PER_N if per_n else 0)
+        rc, handle = _native.ols_batch_plan(list(Ns), list(M), list(F), None if N is None else list(N), flags)
         check(rc, "ols_batch_plan")
         self._h = handle
         self.device = torch.device("cuda", torch.cuda.current_device())

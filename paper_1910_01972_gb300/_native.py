@@ -27,6 +27,7 @@ OLS_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 OLS_FLAG_FP32 = 0
 OLS_TUNE_MODEL = 1 << 8
+OLS_BATCH_PER_N = 1 << 9
 OLS_FLAG_TC_FP16SPLIT = 1
 OLS_FLAG_TC_BF16SPLIT = 2
 OLS_FLAG_R2R = 4

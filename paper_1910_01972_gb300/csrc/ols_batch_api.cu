@@ -28,6 +28,8 @@ struct ols_batch_s {
     unsigned long long *d_tickets = nullptr;
     bool filters_ready = false;
     int last_launches = 0;
+    bool single = false;                      // the whole batch in one persistent launch
+    ols::TwTables tw_all{};                   // single launch: twiddles of every segment length
 };
 
 namespace {
@@ -216,7 +218,66 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
         }
         bt->N[b] = n;
     }
-    // groups by segment length; problems in a group by decreasing F
+    if (!(flags & OLS_BATCH_PER_N)) {
+        // One persistent launch for every problem: items of 8192/N segments (one
+        // per slot of a 512-thread block), the most expensive first (an item's
+        // cost grows with F log2 N).
+        int cap = 0;
+        e = batched_one_prepare(bt->sm_count, &cap);
+        if (e != cudaSuccess) {
+            free_batch(bt);
+            return status_of(e);
+        }
+        bt->single = true;
+        std::vector<BatchProblemDev> probs(B);
+        for (int b = 0; b < B; ++b) {
+            const int l = log2_of(bt->N[b]);
+            BatchProblemDev &d = probs[b];
+            d.Hk = reinterpret_cast<const float4 *>(bt->plans[b]->Hk);
+            d.Ns = bt->Ns[b];
+            d.Nout = bt->Nout[b];
+            d.L = bt->L[b];
+            d.nseg = bt->nseg[b];
+            d.M = bt->M[b];
+            d.F = bt->F[b];
+            d.index = b;
+            d.log2N = l;
+            bt->tw_all.tw[l] = bt->plans[b]->tw;
+        }
+        std::vector<int> order(B);
+        for (int b = 0; b < B; ++b) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            return (long long)bt->F[a] * log2_of(bt->N[a]) > (long long)bt->F[c] * log2_of(bt->N[c]);
+        });
+        std::vector<int2> items;
+        for (int b : order) {
+            const int64_t sl = (int64_t)kBatchOneBlock * 16 / bt->N[b];
+            const int64_t tiles = (bt->nseg[b] + sl - 1) / sl;
+            for (int64_t tl = 0; tl < tiles; ++tl) items.push_back(make_int2(b, (int)tl));
+        }
+        BatchGroup g;
+        g.log2N = 0;
+        g.nitems = (long long)items.size();
+        g.grid = (int)std::min<long long>(g.nitems, cap);
+        e = cudaMalloc(&bt->d_probs, sizeof(BatchProblemDev) * probs.size());
+        if (e == cudaSuccess) e = cudaMalloc(&bt->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
+        if (e == cudaSuccess) e = cudaMalloc(&bt->d_tickets, sizeof(unsigned long long));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(bt->d_probs, probs.data(), sizeof(BatchProblemDev) * probs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !items.empty())
+            e = cudaMemcpy(bt->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_batch(bt);
+            return status_of(e);
+        }
+        g.probs = bt->d_probs;
+        g.items = bt->d_items;
+        g.ticket = bt->d_tickets;
+        bt->groups.push_back(g);
+        *out = bt;
+        return OLS_OK;
+    }
+    // per segment length: one persistent launch per group; problems in a group by decreasing F
     std::vector<int> order(B);
     for (int b = 0; b < B; ++b) order[b] = b;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
@@ -249,6 +310,7 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
             d.M = bt->M[b];
             d.F = bt->F[b];
             d.index = b;
+            d.log2N = l;
             const int pi = (int)(probs.size() - p0);
             probs.push_back(d);
             const int64_t tiles = (bt->nseg[b] + segs - 1) / segs;
@@ -314,6 +376,14 @@ int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_pt
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(batch->d_tickets, 0, sizeof(unsigned long long) * batch->groups.size(), st);
     int launches = 0;
+    if (batch->single) {
+        const BatchGroup &g = batch->groups[0];
+        if (e == cudaSuccess)
+            e = batched_one_launch(g.grid, g.probs, g.items, g.nitems, static_cast<const float2 *const *>(s_ptrs),
+                                   static_cast<float2 *const *>(y_ptrs), g.ticket, batch->tw_all, st);
+        batch->last_launches = e == cudaSuccess ? 1 : 0;
+        return status_of(e);
+    }
     for (size_t gi = 0; gi < batch->groups.size() && e == cudaSuccess; ++gi) {
         e = batched_launch(batch->groups[gi], static_cast<const float2 *const *>(s_ptrs),
                            static_cast<float2 *const *>(y_ptrs), st);

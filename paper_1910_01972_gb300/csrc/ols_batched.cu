@@ -114,4 +114,83 @@ cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, flo
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The whole batch in ONE persistent launch.  Blocks of 512 threads pull items
+// from one ticket; an item is SL = 512 / (N/16) consecutive segments of one
+// problem (one per slot of N/16 threads), so every segment length fills the
+// block and needs the same shared memory (two padded exchange buffers per
+// slot: 139 KB).  The slots of an item run independently: each exchanges
+// under its own named barrier (a warp barrier when a slot is within a warp);
+// the block synchronises only to take the next item.  Each segment is
+// processed exactly as by the plain kernel, so results are bitwise those of
+// per-problem calls.
+template <int LOG2N>
+__device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int tile, const float2 *const *s_ptrs,
+                                               float2 *const *y_ptrs, const float2 *tw, float2 *smem, int &xc) {
+    using G = Geo<LOG2N>;
+    constexpr int SL = kBatchOneBlock / G::T;
+    static_assert(SL <= 15 || G::T <= 32, "one named barrier per slot");
+    const int slot = threadIdx.x / G::T;
+    const int t = threadIdx.x % G::T;
+    float2 *bufs = smem + slot * 2 * G::PADN;
+    const long long seg = (long long)tile * SL + slot;
+    const SegmentBarrier<G::T> bar{1 + slot};
+    ols_segment<LOG2N, TwGlobal, false, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, TwGlobal{tw},
+                                                              y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
+                                                              seg < P.nseg, bufs, t, xc, 0u, bar);
+}
+
+__global__ void __launch_bounds__(kBatchOneBlock, 1)
+ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__restrict__ items, long long nitems,
+                       const float2 *const *__restrict__ s_ptrs, float2 *const *__restrict__ y_ptrs,
+                       unsigned long long *__restrict__ ticket, TwTables tw) {
+    extern __shared__ float4 smem_raw[];
+    __shared__ long long item_sh;
+    float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+    int xc = 0;
+    for (;;) {
+        __syncthreads();                       // every slot is done with the previous item
+        if (threadIdx.x == 0) item_sh = (long long)atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const long long item = item_sh;
+        if (item >= nitems) break;
+        const int2 it = items[item];           // (problem, tile)
+        const BatchProblemDev P = probs[it.x];
+        xc = 0;                                // buffers restart with every item
+        switch (P.log2N) {
+            case 8: batch_one_item<8>(P, it.y, s_ptrs, y_ptrs, tw.tw[8], smem, xc); break;
+            case 9: batch_one_item<9>(P, it.y, s_ptrs, y_ptrs, tw.tw[9], smem, xc); break;
+            case 10: batch_one_item<10>(P, it.y, s_ptrs, y_ptrs, tw.tw[10], smem, xc); break;
+            case 11: batch_one_item<11>(P, it.y, s_ptrs, y_ptrs, tw.tw[11], smem, xc); break;
+            case 12: batch_one_item<12>(P, it.y, s_ptrs, y_ptrs, tw.tw[12], smem, xc); break;
+            case 13: batch_one_item<13>(P, it.y, s_ptrs, y_ptrs, tw.tw[13], smem, xc); break;
+            default: break;
+        }
+    }
+}
+
+// two padded exchange buffers per slot; the same for every N
+constexpr size_t kBatchOneSmem = sizeof(float2) * 2 * (size_t)(kBatchOneBlock * 16 + kBatchOneBlock);
+
+cudaError_t batched_one_prepare(int sm_count, int *grid_cap) {
+    cudaError_t e = cudaFuncSetAttribute(ols_batched_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kBatchOneSmem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_one_kernel, kBatchOneBlock,
+                                                      kBatchOneSmem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *grid_cap = per_sm * sm_count;
+    return cudaSuccess;
+}
+
+cudaError_t batched_one_launch(int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
+                               const float2 *const *s_ptrs, float2 *const *y_ptrs, unsigned long long *ticket,
+                               const TwTables &tw, cudaStream_t st) {
+    ols_batched_one_kernel<<<grid, kBatchOneBlock, kBatchOneSmem, st>>>(probs, items, nitems, s_ptrs, y_ptrs, ticket,
+                                                                         tw);
+    return cudaGetLastError();
+}
+
 }  // namespace ols

@@ -98,8 +98,21 @@ struct BatchProblemDev {
     long long Ns, Nout, L, nseg;
     int M, F;
     int index;            // position in the caller's pointer arrays
-    int pad;
+    int log2N;            // segment length of this problem
 };
+
+// Twiddle tables of every segment length, by log2 N (single-launch batches).
+struct TwTables {
+    const float2 *tw[kMaxLog2N + 1];
+};
+
+// The whole batch in one persistent launch: 512-thread blocks; an item is
+// 8192/N consecutive segments of one problem (one per N/16-thread slot).
+constexpr int kBatchOneBlock = 512;
+cudaError_t batched_one_prepare(int sm_count, int *grid_cap);
+cudaError_t batched_one_launch(int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
+                               const float2 *const *s_ptrs, float2 *const *y_ptrs, unsigned long long *ticket,
+                               const TwTables &tw, cudaStream_t st);
 
 // One persistent launch: every problem of the batch with segment length 2^log2N.
 struct BatchGroup {

@@ -15,12 +15,14 @@ namespace ols {
 
 // XT: the segment spectrum waits in the thread's TMEM lane at column xcol_t
 // (32 columns) instead of registers; implied by TMEM twiddles (columns 96..127).
-template <int LOG2N, class TW, bool XT = std::is_same<TW, TwTmem>::value>
+// BAR: the barrier of the segment's exchanges (the whole CTA by default, or
+// only the segment's own threads).
+template <int LOG2N, class TW, bool XT = std::is_same<TW, TwTmem>::value, class BAR = CtaBarrier>
 __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long long Ns,
                                             const float4 *__restrict__ Hk, const TW &tw,
                                             float2 *__restrict__ y, int M, int F, long long L,
                                             long long Nout, long long seg, bool active, float2 *bufs,
-                                            int t, int &xc, uint32_t xcol_t = 0) {
+                                            int t, int &xc, uint32_t xcol_t = 0, const BAR &bar = BAR{}) {
     using G = Geo<LOG2N>;
     const int lo = M - 1;                      // aliased samples per segment
     const long long start = seg * L;
@@ -35,7 +37,7 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
         for (int k = 0; k < 16; ++k)
             X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
     }
-    forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
+    forward_passes<LOG2N, 0>(X, bufs, tw, t, xc, bar);
     constexpr bool x_in_tmem = XT;
     uint32_t xcol = 0;
     if constexpr (x_in_tmem) {
@@ -91,7 +93,7 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
             x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(h.z, h.w));
         }
 #endif
-        inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
+        inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc, bar);
         float2 *dst = y + (size_t)f * (size_t)Nout;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {

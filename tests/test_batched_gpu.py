@@ -1,6 +1,6 @@
-"""The batched uneven form (persistent launches, work tickets, autotuned
-segment lengths, CUDA-graph capture) against the FP64 oracle and against
-per-problem plain calls."""
+"""The batched uneven form (one persistent launch for the whole batch, or one
+per segment length; work tickets, autotuned segment lengths, CUDA-graph
+capture) against the FP64 oracle and against per-problem plain calls."""
 import numpy as np
 import pytest
 import torch
@@ -38,15 +38,16 @@ def small_inputs(seed=3):
     return ss, hs
 
 
-def test_batched_matches_oracle_and_plain_calls():
+@pytest.mark.parametrize("per_n", [False, True])
+def test_batched_matches_oracle_and_plain_calls(per_n):
     ss, hs = small_inputs()
-    bp = BatchPlan(SMALL["Ns"], SMALL["M"], SMALL["F"], SMALL["N"])
+    bp = BatchPlan(SMALL["Ns"], SMALL["M"], SMALL["F"], SMALL["N"], per_n=per_n)
     assert bp.N == SMALL["N"]
     bp.set_filters([dev(h) for h in hs])
     sd = [dev(s) for s in ss]
     ys = bp.convolve(sd)
     torch.cuda.synchronize()
-    assert bp.last_launch_count() == len(set(SMALL["N"]))
+    assert bp.last_launch_count() == (len(set(SMALL["N"])) if per_n else 1)
     for b in range(bp.B):
         y = ys[b].cpu().numpy()
         assert oracle.max_stream_rel_l2(y, oracle.conv(ss[b], hs[b])) <= TOL, b
@@ -78,9 +79,10 @@ def test_autotune_is_cached_and_model_is_consistent():
     assert nm >= 257 and nm & (nm - 1) == 0
 
 
-def test_graph_capture_and_replay_with_new_data():
+@pytest.mark.parametrize("per_n", [False, True])
+def test_graph_capture_and_replay_with_new_data(per_n):
     ss, hs = small_inputs(5)
-    bp = BatchPlan(SMALL["Ns"], SMALL["M"], SMALL["F"], SMALL["N"])
+    bp = BatchPlan(SMALL["Ns"], SMALL["M"], SMALL["F"], SMALL["N"], per_n=per_n)
     bp.set_filters([dev(h) for h in hs])
     sd = [dev(s) for s in ss]
     ys = bp.outputs()
@@ -107,13 +109,14 @@ def test_graph_capture_and_replay_with_new_data():
     bp.close()
 
 
-def test_full_size_uneven_batch_sampled():
+@pytest.mark.parametrize("per_n", [False, True])
+def test_full_size_uneven_batch_sampled(per_n):
     """64 signals, lengths log-uniform in [2^16, 2^22], F in {8..128},
     M in {33, ..., 1025}, autotuned N: sampled outputs of every problem
     against the oracle, and three problems against plain calls."""
     spec = synth.batch_spec()
     ss, hs = synth.batch_inputs(spec)
-    bp = BatchPlan(spec.Ns, spec.M, spec.F)
+    bp = BatchPlan(spec.Ns, spec.M, spec.F, per_n=per_n)
     bp.set_filters([dev(h) for h in hs])
     sd = [dev(s) for s in ss]
     ys = bp.convolve(sd)
