@@ -15,6 +15,10 @@
 #include "ols.h"
 #include "ols_internal.h"
 
+#ifndef OLS_BATCH_BLOCK256
+#define OLS_BATCH_BLOCK256 1     // single launch: 256-thread blocks when every segment length is <= 4096
+#endif
+
 struct ols_batch_s {
     int device = 0;
     int sm_count = 0;
@@ -29,6 +33,7 @@ struct ols_batch_s {
     bool filters_ready = false;
     int last_launches = 0;
     bool single = false;                      // the whole batch in one persistent launch
+    int one_block = 0;                        // its block size
     ols::TwTables tw_all{};                   // single launch: twiddles of every segment length
 };
 
@@ -223,7 +228,10 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
         // per slot of a 512-thread block), the most expensive first (an item's
         // cost grows with F log2 N).
         int cap = 0;
-        e = batched_one_prepare(bt->sm_count, &cap);
+        int64_t maxN = 0;
+        for (int b = 0; b < B; ++b) maxN = std::max<int64_t>(maxN, bt->N[b]);
+        bt->one_block = (maxN <= 4096 && OLS_BATCH_BLOCK256) ? 256 : 512;
+        e = batched_one_prepare(bt->one_block, bt->sm_count, &cap);
         if (e != cudaSuccess) {
             free_batch(bt);
             return status_of(e);
@@ -251,7 +259,7 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
         });
         std::vector<int2> items;
         for (int b : order) {
-            const int64_t sl = (int64_t)kBatchOneBlock * 16 / bt->N[b];
+            const int64_t sl = (int64_t)bt->one_block * 16 / bt->N[b];
             const int64_t tiles = (bt->nseg[b] + sl - 1) / sl;
             for (int64_t tl = 0; tl < tiles; ++tl) items.push_back(make_int2(b, (int)tl));
         }
@@ -379,7 +387,8 @@ int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_pt
     if (batch->single) {
         const BatchGroup &g = batch->groups[0];
         if (e == cudaSuccess)
-            e = batched_one_launch(g.grid, g.probs, g.items, g.nitems, static_cast<const float2 *const *>(s_ptrs),
+            e = batched_one_launch(batch->one_block, g.grid, g.probs, g.items, g.nitems,
+                                   static_cast<const float2 *const *>(s_ptrs),
                                    static_cast<float2 *const *>(y_ptrs), g.ticket, batch->tw_all, st);
         batch->last_launches = e == cudaSuccess ? 1 : 0;
         return status_of(e);

@@ -124,23 +124,26 @@ cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, flo
 // the block synchronises only to take the next item.  Each segment is
 // processed exactly as by the plain kernel, so results are bitwise those of
 // per-problem calls.
-template <int LOG2N>
+template <int BB, int LOG2N>
 __device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int tile, const float2 *const *s_ptrs,
                                                float2 *const *y_ptrs, const float2 *tw, float2 *smem, int &xc) {
     using G = Geo<LOG2N>;
-    constexpr int SL = kBatchOneBlock / G::T;
-    static_assert(SL <= 15 || G::T <= 32, "one named barrier per slot");
-    const int slot = threadIdx.x / G::T;
-    const int t = threadIdx.x % G::T;
-    float2 *bufs = smem + slot * 2 * G::PADN;
-    const long long seg = (long long)tile * SL + slot;
-    const SegmentBarrier<G::T> bar{1 + slot};
-    ols_segment<LOG2N, TwGlobal, false, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, TwGlobal{tw},
-                                                              y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
-                                                              seg < P.nseg, bufs, t, xc, 0u, bar);
+    if constexpr (G::T <= BB) {
+        constexpr int SL = BB / G::T;
+        static_assert(SL <= 15 || G::T <= 32, "one named barrier per slot");
+        const int slot = threadIdx.x / G::T;
+        const int t = threadIdx.x % G::T;
+        float2 *bufs = smem + slot * 2 * G::PADN;
+        const long long seg = (long long)tile * SL + slot;
+        const SegmentBarrier<G::T> bar{1 + slot};
+        ols_segment<LOG2N, TwGlobal, false, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, TwGlobal{tw},
+                                                                  y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
+                                                                  seg < P.nseg, bufs, t, xc, 0u, bar);
+    }
 }
 
-__global__ void __launch_bounds__(kBatchOneBlock, 1)
+template <int BB>
+__global__ void __launch_bounds__(BB, kBatchOneBlock / BB)
 ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__restrict__ items, long long nitems,
                        const float2 *const *__restrict__ s_ptrs, float2 *const *__restrict__ y_ptrs,
                        unsigned long long *__restrict__ ticket, TwTables tw) {
@@ -158,38 +161,51 @@ ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__
         const BatchProblemDev P = probs[it.x];
         xc = 0;                                // buffers restart with every item
         switch (P.log2N) {
-            case 8: batch_one_item<8>(P, it.y, s_ptrs, y_ptrs, tw.tw[8], smem, xc); break;
-            case 9: batch_one_item<9>(P, it.y, s_ptrs, y_ptrs, tw.tw[9], smem, xc); break;
-            case 10: batch_one_item<10>(P, it.y, s_ptrs, y_ptrs, tw.tw[10], smem, xc); break;
-            case 11: batch_one_item<11>(P, it.y, s_ptrs, y_ptrs, tw.tw[11], smem, xc); break;
-            case 12: batch_one_item<12>(P, it.y, s_ptrs, y_ptrs, tw.tw[12], smem, xc); break;
-            case 13: batch_one_item<13>(P, it.y, s_ptrs, y_ptrs, tw.tw[13], smem, xc); break;
+            case 8: batch_one_item<BB, 8>(P, it.y, s_ptrs, y_ptrs, tw.tw[8], smem, xc); break;
+            case 9: batch_one_item<BB, 9>(P, it.y, s_ptrs, y_ptrs, tw.tw[9], smem, xc); break;
+            case 10: batch_one_item<BB, 10>(P, it.y, s_ptrs, y_ptrs, tw.tw[10], smem, xc); break;
+            case 11: batch_one_item<BB, 11>(P, it.y, s_ptrs, y_ptrs, tw.tw[11], smem, xc); break;
+            case 12: batch_one_item<BB, 12>(P, it.y, s_ptrs, y_ptrs, tw.tw[12], smem, xc); break;
+            case 13: batch_one_item<BB, 13>(P, it.y, s_ptrs, y_ptrs, tw.tw[13], smem, xc); break;
             default: break;
         }
     }
 }
 
 // two padded exchange buffers per slot; the same for every N
-constexpr size_t kBatchOneSmem = sizeof(float2) * 2 * (size_t)(kBatchOneBlock * 16 + kBatchOneBlock);
+template <int BB>
+constexpr size_t batch_one_smem() { return sizeof(float2) * 2 * (size_t)(BB * 16 + BB); }
 
-cudaError_t batched_one_prepare(int sm_count, int *grid_cap) {
-    cudaError_t e = cudaFuncSetAttribute(ols_batched_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kBatchOneSmem);
+template <int BB>
+static cudaError_t batched_one_prepare_b(int sm_count, int *grid_cap) {
+    cudaError_t e = cudaFuncSetAttribute(ols_batched_one_kernel<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_one_smem<BB>());
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_one_kernel, kBatchOneBlock,
-                                                      kBatchOneSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_one_kernel<BB>, BB, batch_one_smem<BB>());
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *grid_cap = per_sm * sm_count;
     return cudaSuccess;
 }
 
-cudaError_t batched_one_launch(int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
+cudaError_t batched_one_prepare(int block, int sm_count, int *grid_cap) {
+    if (block == 256) return batched_one_prepare_b<256>(sm_count, grid_cap);
+    if (block == 512) return batched_one_prepare_b<512>(sm_count, grid_cap);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
                                const float2 *const *s_ptrs, float2 *const *y_ptrs, unsigned long long *ticket,
                                const TwTables &tw, cudaStream_t st) {
-    ols_batched_one_kernel<<<grid, kBatchOneBlock, kBatchOneSmem, st>>>(probs, items, nitems, s_ptrs, y_ptrs, ticket,
-                                                                         tw);
+    if (block == 256)
+        ols_batched_one_kernel<256><<<grid, 256, batch_one_smem<256>(), st>>>(probs, items, nitems, s_ptrs, y_ptrs,
+                                                                            ticket, tw);
+    else if (block == 512)
+        ols_batched_one_kernel<512><<<grid, 512, batch_one_smem<512>(), st>>>(probs, items, nitems, s_ptrs, y_ptrs,
+                                                                            ticket, tw);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

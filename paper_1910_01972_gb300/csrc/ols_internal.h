@@ -106,11 +106,12 @@ struct TwTables {
     const float2 *tw[kMaxLog2N + 1];
 };
 
-// The whole batch in one persistent launch: 512-thread blocks; an item is
-// 8192/N consecutive segments of one problem (one per N/16-thread slot).
-constexpr int kBatchOneBlock = 512;
-cudaError_t batched_one_prepare(int sm_count, int *grid_cap);
-cudaError_t batched_one_launch(int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
+// The whole batch in one persistent launch: blocks of `block` threads (256 when
+// every N <= 4096, else 512); an item is block * 16 / N consecutive segments of
+// one problem (one per N/16-thread slot).
+constexpr int kBatchOneBlock = 512;   // largest block (N = 8192 needs 512 threads)
+cudaError_t batched_one_prepare(int block, int sm_count, int *grid_cap);
+cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
                                const float2 *const *s_ptrs, float2 *const *y_ptrs, unsigned long long *ticket,
                                const TwTables &tw, cudaStream_t st);
 
