@@ -318,8 +318,8 @@ OLS_API int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N);
  * A batch of B independent problems of uneven size: signal b has Ns[b]
  * samples, F[b] filters of M[b] taps, segment length N[b] (N == NULL or
  * N[b] == 0: ols_autotune(M[b], F[b], flags)).  Host arrays of B entries.
- * The whole batch is ONE persistent launch: its resident blocks (256
- * threads, or 512 when a problem has N = 8192) pull (problem, segment tile)
+ * The whole batch is ONE persistent launch: its resident blocks (N/16
+ * threads for the longest N, at least 128) pull (problem, segment tile)
  * work items from an atomic ticket, the most expensive (F log2 N) first; a
  * tile is (block size x 16)/N segments of one problem, each on a slot of
  * N/16 threads with barriers of its own.  With

@@ -15,8 +15,8 @@
 #include "ols.h"
 #include "ols_internal.h"
 
-#ifndef OLS_BATCH_BLOCK256
-#define OLS_BATCH_BLOCK256 1     // single launch: 256-thread blocks when every segment length is <= 4096
+#ifndef OLS_BATCH_SMALL_BLOCKS
+#define OLS_BATCH_SMALL_BLOCKS 1  // single launch: the smallest block holding the longest segment (else 512)
 #endif
 
 struct ols_batch_s {
@@ -230,7 +230,9 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
         int cap = 0;
         int64_t maxN = 0;
         for (int b = 0; b < B; ++b) maxN = std::max<int64_t>(maxN, bt->N[b]);
-        bt->one_block = (maxN <= 4096 && OLS_BATCH_BLOCK256) ? 256 : 512;
+        // the smallest block that holds a segment of the longest N (16 points per thread)
+        bt->one_block = (int)std::min<int64_t>(512, std::max<int64_t>(128, maxN / 16));
+        if (!OLS_BATCH_SMALL_BLOCKS) bt->one_block = 512;
         e = batched_one_prepare(bt->one_block, bt->sm_count, &cap);
         if (e != cudaSuccess) {
             free_batch(bt);

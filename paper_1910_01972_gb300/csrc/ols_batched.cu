@@ -190,6 +190,7 @@ static cudaError_t batched_one_prepare_b(int sm_count, int *grid_cap) {
 }
 
 cudaError_t batched_one_prepare(int block, int sm_count, int *grid_cap) {
+    if (block == 128) return batched_one_prepare_b<128>(sm_count, grid_cap);
     if (block == 256) return batched_one_prepare_b<256>(sm_count, grid_cap);
     if (block == 512) return batched_one_prepare_b<512>(sm_count, grid_cap);
     return cudaErrorInvalidValue;
@@ -198,7 +199,10 @@ cudaError_t batched_one_prepare(int block, int sm_count, int *grid_cap) {
 cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
                                const float2 *const *s_ptrs, float2 *const *y_ptrs, unsigned long long *ticket,
                                const TwTables &tw, cudaStream_t st) {
-    if (block == 256)
+    if (block == 128)
+        ols_batched_one_kernel<128><<<grid, 128, batch_one_smem<128>(), st>>>(probs, items, nitems, s_ptrs, y_ptrs,
+                                                                            ticket, tw);
+    else if (block == 256)
         ols_batched_one_kernel<256><<<grid, 256, batch_one_smem<256>(), st>>>(probs, items, nitems, s_ptrs, y_ptrs,
                                                                             ticket, tw);
     else if (block == 512)

@@ -106,9 +106,9 @@ struct TwTables {
     const float2 *tw[kMaxLog2N + 1];
 };
 
-// The whole batch in one persistent launch: blocks of `block` threads (256 when
-// every N <= 4096, else 512); an item is block * 16 / N consecutive segments of
-// one problem (one per N/16-thread slot).
+// The whole batch in one persistent launch: blocks of `block` threads (the
+// longest segment's N/16, at least 128); an item is block * 16 / N consecutive
+// segments of one problem (one per N/16-thread slot).
 constexpr int kBatchOneBlock = 512;   // largest block (N = 8192 needs 512 threads)
 cudaError_t batched_one_prepare(int block, int sm_count, int *grid_cap);
 cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,

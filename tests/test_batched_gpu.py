@@ -135,3 +135,28 @@ def test_full_size_uneven_batch_sampled(per_n):
         assert torch.equal(p.convolve(sd[b]), ys[b])
         p.close()
     bp.close()
+
+
+def test_single_launch_block_sizes_cover_every_segment_length():
+    """The single launch picks its block from the longest segment (N/16
+    threads, at least 128): a batch with N <= 2048 runs 128-thread blocks, one
+    with N = 4096 256-thread blocks, one with N = 8192 512-thread blocks (the
+    test above).  Each is bitwise equal to per-problem calls."""
+    g = np.random.Generator(np.random.PCG64(21))
+    for Ns_, M_, F_, N_ in (([5_000, 40_000, 300, 77_777], [33, 200, 65, 129], [3, 2, 4, 5], [256, 512, 1024, 2048]),
+                            ([50_000, 9_000, 60_001], [1000, 17, 300], [2, 6, 3], [4096, 256, 2048])):
+        ss = [synth.signal(g, n) for n in Ns_]
+        hs = [synth.filters(g, f, m) for f, m in zip(F_, M_)]
+        bp = BatchPlan(Ns_, M_, F_, N_)
+        bp.set_filters([dev(h) for h in hs])
+        sd = [dev(s) for s in ss]
+        ys = bp.convolve(sd)
+        torch.cuda.synchronize()
+        assert bp.last_launch_count() == 1
+        for b in range(bp.B):
+            p = Plan(M_[b], F_[b], N_[b])
+            p.set_filters(dev(hs[b]))
+            assert torch.equal(p.convolve(sd[b]), ys[b]), (N_, b)
+            p.close()
+            assert oracle.max_stream_rel_l2(ys[b].cpu().numpy(), oracle.conv(ss[b], hs[b])) <= TOL
+        bp.close()
