@@ -71,7 +71,10 @@ static cudaError_t batched_prepare_n(int sm_count, int *grid_cap, int *segs) {
                                          (int)G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM);
+    if (OLS_FWD_TW_TMEM)
+        e = resident_blocks_tmem(ols_batched_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM, (int)G::TMEM_COLS, &per_sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (OLS_FWD_TW_TMEM && per_sm > G::TMEM_MAX_CTAS) per_sm = G::TMEM_MAX_CTAS;
@@ -126,7 +129,8 @@ cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, flo
 // per-problem calls.
 template <int BB, int LOG2N>
 __device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int tile, const float2 *const *s_ptrs,
-                                               float2 *const *y_ptrs, const float2 *tw, float2 *smem, int &xc) {
+                                               float2 *const *y_ptrs, const float2 *tw, float2 *smem, int &xc,
+                                               uint32_t tbase) {
     using G = Geo<LOG2N>;
     if constexpr (G::T <= BB) {
         constexpr int SL = BB / G::T;
@@ -136,9 +140,20 @@ __device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int til
         float2 *bufs = smem + slot * 2 * G::PADN;
         const long long seg = (long long)tile * SL + slot;
         const SegmentBarrier<G::T> bar{1 + slot};
+#if OLS_FWD_TW_TMEM
+        // the same TMEM layout as the plain kernel (twiddles of this N, then the
+        // segment spectrum), so results stay bitwise those of per-problem calls
+        const TwTmem twt{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+        tw_tmem_fill<LOG2N>(tw, twt.base, t);
+        ols_segment<LOG2N, TwTmem, true, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, twt, y_ptrs[P.index],
+                                                               P.M, P.F, P.L, P.Nout, seg, seg < P.nseg, bufs, t, xc,
+                                                               0u, bar);
+#else
+        (void)tbase;
         ols_segment<LOG2N, TwGlobal, false, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, TwGlobal{tw},
                                                                   y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
                                                                   seg < P.nseg, bufs, t, xc, 0u, bar);
+#endif
     }
 }
 
@@ -149,7 +164,17 @@ ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__
                        unsigned long long *__restrict__ ticket, TwTables tw) {
     extern __shared__ float4 smem_raw[];
     __shared__ long long item_sh;
+    __shared__ uint32_t tbase;
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+#if OLS_FWD_TW_TMEM
+    constexpr uint32_t kCols = (uint32_t)(BB / 128) * 128u;   // a 128-column lane range per 128 threads
+    if (threadIdx.x < 32) tmem::alloc(&tbase, kCols);
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+#else
+    tbase = 0;
+#endif
     int xc = 0;
     for (;;) {
         __syncthreads();                       // every slot is done with the previous item
@@ -161,15 +186,21 @@ ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__
         const BatchProblemDev P = probs[it.x];
         xc = 0;                                // buffers restart with every item
         switch (P.log2N) {
-            case 8: batch_one_item<BB, 8>(P, it.y, s_ptrs, y_ptrs, tw.tw[8], smem, xc); break;
-            case 9: batch_one_item<BB, 9>(P, it.y, s_ptrs, y_ptrs, tw.tw[9], smem, xc); break;
-            case 10: batch_one_item<BB, 10>(P, it.y, s_ptrs, y_ptrs, tw.tw[10], smem, xc); break;
-            case 11: batch_one_item<BB, 11>(P, it.y, s_ptrs, y_ptrs, tw.tw[11], smem, xc); break;
-            case 12: batch_one_item<BB, 12>(P, it.y, s_ptrs, y_ptrs, tw.tw[12], smem, xc); break;
-            case 13: batch_one_item<BB, 13>(P, it.y, s_ptrs, y_ptrs, tw.tw[13], smem, xc); break;
+            case 8: batch_one_item<BB, 8>(P, it.y, s_ptrs, y_ptrs, tw.tw[8], smem, xc, tbase); break;
+            case 9: batch_one_item<BB, 9>(P, it.y, s_ptrs, y_ptrs, tw.tw[9], smem, xc, tbase); break;
+            case 10: batch_one_item<BB, 10>(P, it.y, s_ptrs, y_ptrs, tw.tw[10], smem, xc, tbase); break;
+            case 11: batch_one_item<BB, 11>(P, it.y, s_ptrs, y_ptrs, tw.tw[11], smem, xc, tbase); break;
+            case 12: batch_one_item<BB, 12>(P, it.y, s_ptrs, y_ptrs, tw.tw[12], smem, xc, tbase); break;
+            case 13: batch_one_item<BB, 13>(P, it.y, s_ptrs, y_ptrs, tw.tw[13], smem, xc, tbase); break;
             default: break;
         }
     }
+#if OLS_FWD_TW_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, kCols);
+#endif
 }
 
 // two padded exchange buffers per slot; the same for every N
@@ -182,7 +213,11 @@ static cudaError_t batched_one_prepare_b(int sm_count, int *grid_cap) {
                                          (int)batch_one_smem<BB>());
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_one_kernel<BB>, BB, batch_one_smem<BB>());
+    if (OLS_FWD_TW_TMEM)
+        e = resident_blocks_tmem(ols_batched_one_kernel<BB>, BB, batch_one_smem<BB>(), (BB / 128) * 128, &per_sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_batched_one_kernel<BB>, BB,
+                                                          batch_one_smem<BB>());
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *grid_cap = per_sm * sm_count;

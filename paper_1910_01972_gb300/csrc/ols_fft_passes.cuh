@@ -19,6 +19,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "fft_regs.cuh"
 #include "tmem.cuh"
@@ -37,7 +38,10 @@
 #define OLS_TW_GLOBAL 1      // twiddles read through L1 (1) or staged in shared memory (0)
 #endif
 #ifndef OLS_FWD_TW_TMEM
-#define OLS_FWD_TW_TMEM 0    // 1: fused kernels keep twiddles and the segment spectrum in TMEM
+#define OLS_FWD_TW_TMEM 1    // fused kernels keep twiddles and the segment spectrum in TMEM (0: registers and L1)
+#endif
+#ifndef OLS_TW_TMEM_LATE
+#define OLS_TW_TMEM_LATE 0   // 1: TMEM twiddles of an inverse pass are read after its exchange, not before
 #endif
 #ifndef OLS_FWD_X_TMEM
 #define OLS_FWD_X_TMEM 0     // 1: the forward kernel keeps only the segment spectrum in TMEM
@@ -270,9 +274,13 @@ __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const TW
     using G = Geo<LOG2N>;
     if constexpr (P < G::NP - 1) {
         typename TW::Fetched f;
-        tw.template fetch<LOG2N, P>(f, t);            // in flight during the exchange
+        // in flight during the exchange, except TMEM twiddles with OLS_TW_TMEM_LATE
+        // (their 30 registers then are not live across the exchange)
+        constexpr bool late = OLS_TW_TMEM_LATE && std::is_same<TW, TwTmem>::value;
+        if constexpr (!late) tw.template fetch<LOG2N, P>(f, t);
         exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t, bar);
         ++xc;
+        if constexpr (late) tw.template fetch<LOG2N, P>(f, t);
         tw.template apply<true>(x, f);
     }
     dft_groups<G::radix(P), true>(x);

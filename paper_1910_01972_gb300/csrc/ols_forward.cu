@@ -103,7 +103,11 @@ static cudaError_t prepare_one(ols_plan_s &p) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_forward_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM);
+    if (OLS_FWD_TW_TMEM || OLS_FWD_X_TMEM)
+        e = resident_blocks_tmem(ols_forward_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM,
+                                 OLS_FWD_TW_TMEM ? (int)G::TMEM_COLS : (int)G::XT_COLS, &per_sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_forward_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (OLS_FWD_TW_TMEM && per_sm > G::TMEM_MAX_CTAS) per_sm = G::TMEM_MAX_CTAS;

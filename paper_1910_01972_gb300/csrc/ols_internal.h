@@ -42,6 +42,40 @@ struct Staging {            // device buffers of ols_convolve_host
     cudaEvent_t ev_user = nullptr, ev_done[2] = {nullptr, nullptr};
 };
 
+// Resident blocks per SM of a kernel that allocates `tmem_cols` TMEM columns
+// per block, from the SM's limits themselves (registers per sub-partition,
+// shared memory, threads, blocks, the 512 TMEM columns): the runtime's
+// occupancy query answers 1 for any kernel that allocates tensor memory,
+// which would leave half or more of the SMs' warp slots empty.
+template <class KERNEL>
+cudaError_t resident_blocks_tmem(KERNEL kernel, int block, size_t dyn_smem, int tmem_cols, int *per_sm) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, blk_sm = 0, reserved = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess) return e;
+    const int warps = (block + 31) / 32;
+    const int warp_regs = ((a.numRegs * 32 + 255) / 256) * 256;      // allocated per warp in 256-register units
+    const int per_part = warp_regs > 0 ? (regs_sm / 4) / warp_regs : 64; // warps one sub-partition holds
+    const int by_regs = per_part / ((warps + 3) / 4);                     // a block spreads over 4 sub-partitions
+    const size_t blk_smem = ((dyn_smem + a.sharedSizeBytes + (size_t)reserved + 127) / 128) * 128;
+    const int by_smem = blk_smem ? (int)((size_t)smem_sm / blk_smem) : blk_sm;
+    const int by_thr = thr_sm / block;
+    const int by_tmem = tmem_cols > 0 ? 512 / tmem_cols : blk_sm;
+    int n = by_regs;
+    if (by_smem < n) n = by_smem;
+    if (by_thr < n) n = by_thr;
+    if (blk_sm < n) n = blk_sm;
+    if (by_tmem < n) n = by_tmem;
+    *per_sm = n;
+    return cudaSuccess;
+}
+
 }  // namespace ols
 
 struct ols_plan_s {

@@ -227,7 +227,10 @@ static cudaError_t pair_prepare_n(ols_plan_s &p) {
                                          (int)PG::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_pair_kernel<LOG2N>, PG::BLOCK, PG::SMEM);
+    if (OLS_PAIR_X_TMEM)
+        e = resident_blocks_tmem(ols_pair_kernel<LOG2N>, PG::BLOCK, PG::SMEM, 64, &per_sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_pair_kernel<LOG2N>, PG::BLOCK, PG::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     p.pair_grid_cap = per_sm * p.sm_count;

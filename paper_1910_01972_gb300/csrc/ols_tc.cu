@@ -326,12 +326,10 @@ static cudaError_t tc_prepare_one(ols_plan_s &p) {
                                          (int)TcGeo<LOG2N>::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_tc_kernel<LOG2N, BF16>, Geo<LOG2N>::BLOCK,
-                                                      TcGeo<LOG2N>::SMEM);
+    const int cols = (Geo<LOG2N>::BLOCK / 128) * tc::kCols;   // TMEM holds every resident CTA's columns
+    e = resident_blocks_tmem(ols_tc_kernel<LOG2N, BF16>, Geo<LOG2N>::BLOCK, TcGeo<LOG2N>::SMEM, cols, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int cols = (Geo<LOG2N>::BLOCK / 128) * tc::kCols;
-    if (per_sm * cols > 512) per_sm = 512 / cols;         // TMEM holds every resident CTA's columns
     p.tc_grid_cap = per_sm * p.sm_count;
     return cudaSuccess;
 }

@@ -217,10 +217,9 @@ cudaError_t w64_prepare(ols_plan_s &p) {
                                          (int)w64::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_w64_kernel, w64::THREADS, w64::SMEM);
+    e = resident_blocks_tmem(ols_w64_kernel, w64::THREADS, w64::SMEM, (int)w64::NCOLS, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (per_sm > 2) per_sm = 2;                       // 2 x 256 TMEM columns
     p.w64_grid_cap = per_sm * p.sm_count;
     return cudaSuccess;
 }
