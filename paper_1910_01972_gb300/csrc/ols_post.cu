@@ -22,6 +22,7 @@
 
 #include "ols_fft_passes.cuh"
 #include "ols_internal.h"
+#include "tmem.cuh"
 
 namespace ols {
 
@@ -44,12 +45,25 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
     using G = Geo<LOG2N>;
     using PG = PostGeo<LOG2N, MODE>;
     extern __shared__ float4 smem_raw[];
+    __shared__ uint32_t tbase;
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
     float2 *bufs = smem + slot * PG::BUFS * G::PADN;
     float2 *dbuf = bufs + G::XBUFS * G::PADN;        // DERIV: the output's neighbourhood
+#if OLS_FWD_TW_TMEM
+    // the forward kernel's TMEM layout: twiddles, then the segment spectrum (columns 96..127)
+    if (threadIdx.x < 32) tmem::alloc(&tbase, G::TMEM_COLS);
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N>(twg, tw.base, t);
+    const uint32_t xcol = tw.base + 96;
+#else
+    (void)tbase;
     const TwGlobal tw{twg};
+#endif
     // circular position of a segment's first output, and its input offset
     const int n0 = MODE == POST_DERIV ? M : M - 1;
     const long long off = MODE == POST_DERIV ? -1 : 0;
@@ -75,6 +89,10 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
             }
         }
         forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
+#if OLS_FWD_TW_TMEM
+        tmem::st32(xcol, reinterpret_cast<const float *>(X));
+        tmem::wait_st();
+#endif
 
         const long long rem = active ? (Nout - j0) : 0;
         const int span = (int)(rem < step ? rem : step);
@@ -84,10 +102,17 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
         for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
         for (int f = 0; f < F; ++f) {
             float2 x[16];
+#if OLS_FWD_TW_TMEM
+            tmem::ld32(xcol, reinterpret_cast<float *>(x));
+            tmem::wait_ld();
+#else
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = X[j];
+#endif
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2) {
-                x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].y));
-                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
+                x[2 * j2] = cmul(x[2 * j2], make_float2(hn[j2].x, hn[j2].y));
+                x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
             }
             if (f + 1 < F) {
                 const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
@@ -154,6 +179,12 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
             }
         }
     }
+#if OLS_FWD_TW_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, G::TMEM_COLS);
+#endif
 }
 
 template <int LOG2N, int MODE>
@@ -164,7 +195,10 @@ static cudaError_t post_prepare_nm(ols_plan_s &p) {
                                          (int)PG::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_post_kernel<LOG2N, MODE>, G::BLOCK, PG::SMEM);
+    if (OLS_FWD_TW_TMEM)
+        e = resident_blocks_tmem(ols_post_kernel<LOG2N, MODE>, G::BLOCK, PG::SMEM, (int)G::TMEM_COLS, &per_sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_post_kernel<LOG2N, MODE>, G::BLOCK, PG::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     p.post_grid_cap[MODE] = per_sm * p.sm_count;

@@ -23,6 +23,7 @@
 
 #include "ols_fft_passes.cuh"
 #include "ols_internal.h"
+#include "tmem.cuh"
 
 namespace ols {
 
@@ -54,11 +55,25 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
                long long Nout) {
     using G = Geo<LOG2N>;
     extern __shared__ float4 smem_raw[];
+    __shared__ uint32_t tbase;
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
     float2 *bufs = smem + slot * G::XBUFS * G::PADN;
+#if OLS_FWD_TW_TMEM
+    // the forward kernel's TMEM layout: the thread's twiddles, then (columns
+    // 96..127) the segment spectrum, in its own lane
+    if (threadIdx.x < 32) tmem::alloc(&tbase, G::TMEM_COLS);
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N>(twg, tw.base, t);
+    const uint32_t xcol = tw.base + 96;
+#else
+    (void)tbase;
     const TwGlobal tw{twg};
+#endif
     const int Fc = (F + 1) / 2;
     const int lo = M - 1;                      // aliased samples per segment
     int xc = 0;
@@ -79,6 +94,10 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
                 X[k] = make_float2((k * G::T + t < lim) ? __ldg(src + k * G::T) : 0.f, 0.f);
         }
         forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
+#if OLS_FWD_TW_TMEM
+        tmem::st32(xcol, reinterpret_cast<const float *>(X));
+        tmem::wait_st();
+#endif
 
         const long long rem = active ? (Nout - start) : 0;
         const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
@@ -89,10 +108,17 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
         for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
         for (int p = 0; p < Fc; ++p) {
             float2 x[16];
+#if OLS_FWD_TW_TMEM
+            tmem::ld32(xcol, reinterpret_cast<float *>(x));
+            tmem::wait_ld();
+#else
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = X[j];
+#endif
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2) {
-                x[2 * j2] = cmul(X[2 * j2], make_float2(hn[j2].x, hn[j2].y));
-                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
+                x[2 * j2] = cmul(x[2 * j2], make_float2(hn[j2].x, hn[j2].y));
+                x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
             }
             if (p + 1 < Fc) {
                 const float4 *hp = Hk + (size_t)(p + 1) * (G::N / 2) + t;
@@ -121,16 +147,25 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
             }
         }
     }
+#if OLS_FWD_TW_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, G::TMEM_COLS);
+#endif
 }
 
 template <int LOG2N>
 static cudaError_t r2r_prepare_n(ols_plan_s &p) {
     using G = Geo<LOG2N>;
     cudaError_t e = cudaFuncSetAttribute(ols_r2r_kernel<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::SMEM);
+                                         (int)G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_r2r_kernel<LOG2N>, G::BLOCK, G::SMEM);
+    if (OLS_FWD_TW_TMEM)
+        e = resident_blocks_tmem(ols_r2r_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM, (int)G::TMEM_COLS, &per_sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_r2r_kernel<LOG2N>, G::BLOCK, G::SMEM_TMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     p.r2r_grid_cap = per_sm * p.sm_count;
@@ -143,7 +178,7 @@ static cudaError_t r2r_launch_n(const ols_plan_s &p, const float *s, int64_t Ns,
     using G = Geo<LOG2N>;
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
     const int grid = (int)(nblk < p.r2r_grid_cap ? nblk : p.r2r_grid_cap);
-    ols_r2r_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM, st>>>(s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y,
+    ols_r2r_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM_TMEM, st>>>(s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y,
                                                            p.M, p.F, L, nseg, Nout);
     return cudaGetLastError();
 }
