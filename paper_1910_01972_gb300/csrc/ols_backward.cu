@@ -35,6 +35,7 @@
 
 #include "ols_fft_passes.cuh"
 #include "ols_internal.h"
+#include "tmem.cuh"
 
 #ifndef OLS_BWD_BLOCK
 #define OLS_BWD_BLOCK 512        // threads per adjoint CTA (slots of N/16 threads), one CTA per SM ...
@@ -47,6 +48,9 @@
 #endif
 #ifndef OLS_BWD_L2HINTS
 #define OLS_BWD_L2HINTS 1        // streamed s and g loads evict first, the per-CTA dh spectra evict last
+#endif
+#ifndef OLS_BWD_TW_TMEM
+#define OLS_BWD_TW_TMEM OLS_FWD_TW_TMEM   // twiddles and the window's signal spectrum A in TMEM
 #endif
 #ifndef OLS_BWD_PREFETCH
 #define OLS_BWD_PREFETCH 1       // pull the next gradient window toward L2 while this one is transformed
@@ -125,9 +129,11 @@ struct BwdGeo {
     static constexpr int BLOCK = SLOTS * G::T;
     static_assert(SLOTS <= 15 || G::T <= 32, "one named barrier per slot");
     static constexpr int HALF = G::N / 2;      // float4 entries of one spectrum
-    // exchange buffers of every slot, then each slot's signal spectrum A
+    // exchange buffers of every slot, then each slot's signal spectrum A (in
+    // TMEM instead with OLS_BWD_TW_TMEM)
     static constexpr size_t XBYTES = sizeof(float2) * (size_t)SLOTS * G::XBUFS * G::PADN;
-    static constexpr size_t SMEM = XBYTES + sizeof(float4) * (size_t)SLOTS * HALF;
+    static constexpr size_t SMEM = XBYTES + (OLS_BWD_TW_TMEM ? 0 : sizeof(float4) * (size_t)SLOTS * HALF);
+    static constexpr uint32_t TMEM_COLS = (uint32_t)(BLOCK / 128) * 128u;   // a 128-column lane range per 128 threads
     static_assert(G::XBUFS == 2, "the product buffer is the exchange buffer not in use");
 };
 
@@ -144,9 +150,22 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
     const int t = threadIdx.x % G::T;
     float2 *const xbase = reinterpret_cast<float2 *>(smem_raw);
     float2 *bufs = xbase + slot * G::XBUFS * G::PADN;
-    float4 *Asm = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES) + slot * BG::HALF;
     const SegmentBarrier<G::T> bar{1 + slot};
+#if OLS_BWD_TW_TMEM
+    // the forward kernel's TMEM layout: the thread's twiddles, then (columns
+    // 96..127) the window's signal spectrum A, in its own lane
+    __shared__ uint32_t tbase;
+    if (threadIdx.x < 32) tmem::alloc(&tbase, BG::TMEM_COLS);
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N>(twg, tw.base, t);
+    const uint32_t acol = tw.base + 96;
+#else
+    float4 *Asm = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES) + slot * BG::HALF;
     const TwGlobal tw{twg};
+#endif
     const L2Hints l2 = L2Hints::make();
     const int lo = M - 1;
     const int Li = (int)L;
@@ -167,10 +186,15 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             for (int k = 0; k < 16; ++k)
                 A[k] = (k * G::T + t < lim) ? ld_stream(sig + start + k * G::T + t, l2) : make_float2(0.f, 0.f);
             forward_passes<LOG2N, 0>(A, bufs, tw, t, xc, bar);
+#if OLS_BWD_TW_TMEM
+            tmem::st32(acol, reinterpret_cast<const float *>(A));
+            tmem::wait_st();
+#else
             // kept in shared memory (the thread's own entries) rather than 32 registers
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2)
                 Asm[j2 * G::T + t] = make_float4(A[2 * j2].x, A[2 * j2].y, A[2 * j2 + 1].x, A[2 * j2 + 1].y);
+#endif
         }
         float2 D[16];
         if constexpr (WANT_DS) {
@@ -209,6 +233,21 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             if constexpr (WANT_DH) {
                 // B_f conj(A) at this thread's storage positions 16 t + j (entries j2 T + t)
                 float4 q[8];
+#if OLS_BWD_TW_TMEM
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {               // A in two 16-column halves
+                    float a[16];
+                    tmem::ld16(acol + 16 * h, a);
+                    tmem::wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int j2 = 4 * h + i;
+                        const float2 q0 = cmulc(b[2 * j2], make_float2(a[4 * i], a[4 * i + 1]));
+                        const float2 q1 = cmulc(b[2 * j2 + 1], make_float2(a[4 * i + 2], a[4 * i + 3]));
+                        q[j2] = make_float4(q0.x, q0.y, q1.x, q1.y);
+                    }
+                }
+#else
 #pragma unroll
                 for (int j2 = 0; j2 < 8; ++j2) {
                     const float4 a = Asm[j2 * G::T + t];
@@ -216,6 +255,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
                     const float2 q1 = cmulc(b[2 * j2 + 1], make_float2(a.z, a.w));
                     q[j2] = make_float4(q0.x, q0.y, q1.x, q1.y);
                 }
+#endif
                 float4 *Pf = Pc + (size_t)f * BG::HALF;
                 if constexpr (BG::SLOTS == 1) {
 #pragma unroll
@@ -263,6 +303,12 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             }
         }
     }
+#if OLS_BWD_TW_TMEM
+    tmem::fence_before_sync();
+    __syncthreads();
+    tmem::fence_after_sync();
+    if (threadIdx.x < 32) tmem::dealloc(tbase, BG::TMEM_COLS);
+#endif
 }
 
 // ds overlaps: ds[b L + u] = head_b[u] + tail_{b-1}[u] for b in [0, nseg],
@@ -371,8 +417,11 @@ static cudaError_t prepare_bwd_one(ols_plan_s &p, int idx) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_backward_kernel<LOG2N, DS, DH>, BG::BLOCK,
-                                                      BG::SMEM);
+    if (OLS_BWD_TW_TMEM)
+        e = resident_blocks_tmem(ols_backward_kernel<LOG2N, DS, DH>, BG::BLOCK, BG::SMEM, (int)BG::TMEM_COLS, &per_sm);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ols_backward_kernel<LOG2N, DS, DH>, BG::BLOCK,
+                                                          BG::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     p.bwd_grid_cap[idx] = per_sm * p.sm_count;
