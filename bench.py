@@ -227,7 +227,7 @@ def measure_others(peak, only=None, ns=0):
     """Throughput of the other workloads on this GPU (outputs and samples for
     oracle checks are returned separately; the oracle runs in the CPU leg).
     `only` restricts the run to one workload (for profiling); `ns` then
-    overrides the differentiable or real-to-real workload's signal length."""
+    overrides the differentiable, real-to-real or tensor-core workload's signal length."""
     import torch
     res, samples = {}, {}
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")       # 256 MB > L2
@@ -243,7 +243,7 @@ def measure_others(peak, only=None, ns=0):
     if want("batched"):
         _batched(res, samples, peak)
     if want("tensor_core"):
-        _tensor_core(res, samples, peak)
+        _tensor_core(res, samples, peak, ns)
     if want("r2r"):
         _r2r(res, samples, peak, ns)
     if want("post"):
@@ -378,13 +378,17 @@ def _batched(res, samples, peak):
     del ys, sd, graph
 
 
-def _tensor_core(res, samples, peak):
-    """Tensor-core split precision vs FP32 on the same inputs."""
+def _tensor_core(res, samples, peak, ns=0):
+    """Tensor-core split precision vs FP32 on the same inputs (`ns` overrides
+    the signal length)."""
+    import dataclasses
     import numpy as np
     import torch
     import synth
     from paper_1910_01972_gb300 import Plan, _native
     cfg = synth.TC_SPLIT
+    if ns:
+        cfg = dataclasses.replace(cfg, Ns=ns, name=cfg.name.replace("Ns16777216", "Ns%d" % ns))
     s_np, h_np = synth.plain_inputs(cfg)
     s = torch.from_numpy(s_np).cuda()
     h = torch.from_numpy(h_np).cuda()
