@@ -159,8 +159,9 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
     tmem::fence_before_sync();
     __syncthreads();
     tmem::fence_after_sync();
-    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-    tw_tmem_fill<LOG2N>(twg, tw.base, t);
+    // without the TMEM exchange: with it the N = 2048 adjoint spills
+    const TwTmemT<false> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N, false>(twg, tw.base, t);
     const uint32_t acol = tw.base + 96;
 #else
     float4 *Asm = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES) + slot * BG::HALF;

@@ -46,6 +46,9 @@
 #ifndef OLS_FWD_X_TMEM
 #define OLS_FWD_X_TMEM 0     // 1: the forward kernel keeps only the segment spectrum in TMEM
 #endif
+#ifndef OLS_TMEM_XCHG
+#define OLS_TMEM_XCHG 1      // N = 2048 segments exchange between their last two passes through TMEM (0: shared memory)
+#endif
 #ifndef OLS_WARPS_PER_SM
 #define OLS_WARPS_PER_SM 16  // resident warps per SM the register budget must allow
 #endif
@@ -70,6 +73,9 @@ struct Geo {
         return o;
     }
     static constexpr int TWN = tw_off(NP - 1);
+    // the exchange between the last two passes goes through TMEM (kernels
+    // with TMEM twiddles; columns 64..95 of the thread's block are free)
+    static constexpr bool TX = OLS_TMEM_XCHG && OLS_FWD_TW_TMEM && LOG2N == 11;
     static constexpr int TWN_PAD = OLS_TW_GLOBAL ? 0 : ((TWN + 1) & ~1);   // keep buffers 16-byte aligned
     static constexpr int XBUFS = OLS_XBUFS;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * XBUFS * PADN);
@@ -135,6 +141,118 @@ __device__ __forceinline__ void exchange(float2 *x, float2 *buf, int t, const BA
     for (int k = 0; k < 16; ++k) x[k] = buf[br + pad_off<LOG2N, PR>(k)];
 }
 
+// ---------------------------------------------------------------------------
+// N = 2048 with the TMEM exchange (Geo<11>::TX).  Positions carry 11 bits
+// p0..p10; pass 0 (radix 16 over p7..p10): thread t = p0..p6, register k =
+// p7..p10; pass 1 (radix 16 over p3..p6): register k = p3..p6, thread lanes
+// (bits 0..4) = (p8, p0, p1, p2, p7), warp = p9, p10; pass 2 (radix 8 over
+// p0..p2): thread = p4..p10, register = p0..p3 (the layout of the spectrum).
+// Between passes 1 and 2 only lane and register bits trade places, inside
+// each warp, which the TMEM shapes do without shared memory or a barrier.
+//
+// Shared-memory exchange of passes 0 and 1: position q at q ^ (p8 << 3)
+// (no padding): conflict-free for both layouts, 16 distinct 8-byte bank
+// pairs per half warp.
+__device__ __forceinline__ int tx11_addr0(int t, int k) { return ((k & 2) ? (t ^ 8) : t) + 128 * k; }
+__device__ __forceinline__ int tx11_addr1(int t, int k) {
+    const int base = ((t >> 1) & 7) + 128 * ((t >> 4) & 1) + 256 * (t & 1) + 512 * (t >> 5);
+    return base + 8 * ((k & 1) ^ (t & 1)) + 16 * (k >> 1);
+}
+template <int P>
+__device__ __forceinline__ int tx11_addr(int t, int k) {
+    if constexpr (P == 0) return tx11_addr0(t, k);
+    else return tx11_addr1(t, k);
+}
+template <int PW, int PR, class BAR>
+__device__ __forceinline__ void exchange_tx11(float2 *x, float2 *buf, int t, const BAR &bar) {
+    if constexpr (Geo<11>::XBUFS == 1) bar();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) buf[tx11_addr<PW>(t, k)] = x[k];
+    bar();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = buf[tx11_addr<PR>(t, k)];
+}
+
+// Pass 1 -> pass 2 inside the warp, through 32 TMEM columns at xb (lane
+// field = the warp's quarter), as two round trips:
+//  1. 16x32bx2 stores, half offset 4 (lane = (p8, p0, p1, p2, p3), column =
+//     (re/im, p6, p7, p4, p5)); 16x256b loads: thread lanes (p6, p7, p8, p0,
+//     p1), registers z[p3][4 (p4 + 2 p5) + 2 p2 + re/im];
+//  2. a 32x32b store (column = (re/im, p4, p5, p2, p3)); 16x256b loads:
+//     thread lanes (p4..p8), x[p0 + 2 p1 + 4 p2 + 8 p3] from
+//     w[p1][4 (p2 + 2 p3) + 2 p0 + re/im].
+__device__ __forceinline__ void tx11_forward(float2 *x, uint32_t xb) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)      // k = p3 + 2 p4 + 4 p5; registers (x[k], x[k + 8]) differ in p6
+        tmem::st16x32bx2_x4<4>(xb + ((uint32_t)(k & 1) << 20) + 8u * ((k >> 1) & 1) + 16u * (k >> 2), x[k].x,
+                               x[k].y, x[k + 8].x, x[k + 8].y);
+    tmem::wait_st();
+    __syncwarp();
+    float z[2][16];
+    tmem::ld16x256b_x4(xb, z[0]);
+    tmem::ld16x256b_x4(xb + (16u << 16), z[1]);
+    tmem::wait_ld();
+    float v[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {   // m = re/im + 2 (p2 + 2 p3 + 4 p4 + 8 p5)
+        const int e = m & 1, p2 = (m >> 1) & 1, p3 = (m >> 2) & 1, p4 = (m >> 3) & 1, p5 = (m >> 4) & 1;
+        v[2 * (p4 + 2 * p5 + 4 * p2 + 8 * p3) + e] = z[p3][4 * (p4 + 2 * p5) + 2 * p2 + e];
+    }
+    tmem::st32(xb, v);
+    tmem::wait_st();
+    __syncwarp();
+    float w[2][16];
+    tmem::ld16x256b_x4(xb, w[0]);
+    tmem::ld16x256b_x4(xb + (16u << 16), w[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {   // k = p0 + 2 p1 + 4 p2 + 8 p3
+        const int p0 = k & 1, p1 = (k >> 1) & 1, p2 = (k >> 2) & 1, p3 = k >> 3;
+        x[k] = make_float2(w[p1][4 * (p2 + 2 * p3) + 2 * p0], w[p1][4 * (p2 + 2 * p3) + 2 * p0 + 1]);
+    }
+}
+// The reverse: pass 2 -> pass 1 (the same round trips backwards).
+__device__ __forceinline__ void tx11_inverse(float2 *x, uint32_t xb) {
+    float w[2][16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int p0 = k & 1, p1 = (k >> 1) & 1, p2 = (k >> 2) & 1, p3 = k >> 3;
+        w[p1][4 * (p2 + 2 * p3) + 2 * p0] = x[k].x;
+        w[p1][4 * (p2 + 2 * p3) + 2 * p0 + 1] = x[k].y;
+    }
+    tmem::st16x256b_x4(xb, w[0]);
+    tmem::st16x256b_x4(xb + (16u << 16), w[1]);
+    tmem::wait_st();
+    __syncwarp();
+    float v[32];
+    tmem::ld32(xb, v);
+    tmem::wait_ld();
+    float z[2][16];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const int e = m & 1, p2 = (m >> 1) & 1, p3 = (m >> 2) & 1, p4 = (m >> 3) & 1, p5 = (m >> 4) & 1;
+        z[p3][4 * (p4 + 2 * p5) + 2 * p2 + e] = v[2 * (p4 + 2 * p5 + 4 * p2 + 8 * p3) + e];
+    }
+    tmem::st16x256b_x4(xb, z[0]);
+    tmem::st16x256b_x4(xb + (16u << 16), z[1]);
+    tmem::wait_st();
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        tmem::ld16x32bx2_x4<4>(xb + ((uint32_t)(k & 1) << 20) + 8u * ((k >> 1) & 1) + 16u * (k >> 2), x[k].x,
+                               x[k].y, x[k + 8].x, x[k + 8].y);
+    tmem::wait_ld();
+}
+
+// Index n' = position mod s of pass P's twiddle W_{16 s}^{n' k} for thread t
+// (XCH: the kernel uses the TMEM exchange, which relabels pass NP-2).
+template <int LOG2N, int P, bool XCH>
+__device__ __forceinline__ int tw_index(int t) {
+    using G = Geo<LOG2N>;
+    if constexpr (XCH && G::TX && P == G::NP - 2) return (t >> 1) & 7;   // lanes 1..3 hold p0..p2
+    else return t % G::stride(P);
+}
+
 // Twiddle sources.  Element k of pass P's 16-point group is multiplied by
 // W_{16 s}^{(t mod s) k} (s = the pass's stride), conjugated for the inverse.
 // Each source splits the step into fetch() (issue the loads) and apply()
@@ -195,10 +313,16 @@ struct TwGlobal {
     }
 };
 
-// TwTmem: the thread's own 15 twiddles of every pass, preloaded into its
+// TwTmemT: the thread's own 15 twiddles of every pass, preloaded into its
 // TMEM lane (pass P at columns 32 P .. 32 P + 29 of `base`): no L1 traffic.
-struct TwTmem {
+// XCH: the segment FFT also uses the TMEM exchange where Geo<>::TX allows it
+// (kernels whose epilogue needs the registers opt out).
+template <bool XCH = true>
+struct TwTmemT {
+    static constexpr bool xchg = XCH;
     uint32_t base;
+    // columns 64..95: the staging area of the TMEM exchange
+    __device__ __forceinline__ uint32_t xbase() const { return base + 64; }
     struct Fetched {
         float v[32];
     };
@@ -214,13 +338,24 @@ struct TwTmem {
     }
 };
 
-// Fill a TwTmem for thread t from the plan's twiddle table.
-template <int LOG2N, int P = 0>
+using TwTmem = TwTmemT<true>;
+template <class TW>
+struct is_tw_tmem : std::false_type {};
+template <bool X>
+struct is_tw_tmem<TwTmemT<X>> : std::true_type {};
+template <class TW>
+__device__ __forceinline__ constexpr bool tw_xchg() {
+    if constexpr (is_tw_tmem<TW>::value) return TW::xchg;
+    else return false;
+}
+
+// Fill a TwTmemT<XCH> for thread t from the plan's twiddle table.
+template <int LOG2N, bool XCH = true, int P = 0>
 __device__ __forceinline__ void tw_tmem_fill(const float2 *tw, uint32_t base, int t) {
     using G = Geo<LOG2N>;
     if constexpr (P < G::NP - 1) {
         constexpr int s = G::stride(P);
-        const float2 *w = tw + G::tw_off(P) + (t % s);
+        const float2 *w = tw + G::tw_off(P) + tw_index<LOG2N, P, XCH>(t);
         float v[32];
 #pragma unroll
         for (int k = 1; k < 16; ++k) {
@@ -230,7 +365,7 @@ __device__ __forceinline__ void tw_tmem_fill(const float2 *tw, uint32_t base, in
         }
         v[30] = v[31] = 0.f;
         tmem::st32(base + 32 * P, v);
-        tw_tmem_fill<LOG2N, P + 1>(tw, base, t);
+        tw_tmem_fill<LOG2N, XCH, P + 1>(tw, base, t);
     } else {
         tmem::wait_st();
     }
@@ -254,8 +389,15 @@ __device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const TW
         tw.template fetch<LOG2N, P>(f, t);            // in flight during the DFT
         dft_groups<G::radix(P), false>(x);
         tw.template apply<false>(x, f);
-        exchange<LOG2N, P, P + 1>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t, bar);
-        ++xc;
+        constexpr bool tx = G::TX && tw_xchg<TW>();
+        if constexpr (tx && P == G::NP - 2) {
+            tx11_forward(x, tw.xbase());
+        } else {
+            float2 *buf = bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0);
+            if constexpr (tx && P + 1 == G::NP - 2) exchange_tx11<P, P + 1>(x, buf, t, bar);
+            else exchange<LOG2N, P, P + 1>(x, buf, t, bar);
+            ++xc;
+        }
         forward_passes<LOG2N, P + 1>(x, bufs, tw, t, xc, bar);
     } else {
         dft_groups<G::radix(P), false>(x);
@@ -275,11 +417,19 @@ __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const TW
     if constexpr (P < G::NP - 1) {
         typename TW::Fetched f;
         // in flight during the exchange, except TMEM twiddles with OLS_TW_TMEM_LATE
-        // (their 30 registers then are not live across the exchange)
-        constexpr bool late = OLS_TW_TMEM_LATE && std::is_same<TW, TwTmem>::value;
+        // or before the TMEM exchange (their 30 registers then are not live
+        // across the exchange: with them the kernel spills)
+        constexpr bool tx = G::TX && tw_xchg<TW>();
+        constexpr bool late = (OLS_TW_TMEM_LATE || (tx && P == G::NP - 2)) && is_tw_tmem<TW>::value;
         if constexpr (!late) tw.template fetch<LOG2N, P>(f, t);
-        exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t, bar);
-        ++xc;
+        if constexpr (tx && P == G::NP - 2) {
+            tx11_inverse(x, tw.xbase());
+        } else {
+            float2 *buf = bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0);
+            if constexpr (tx && P + 1 == G::NP - 2) exchange_tx11<P + 1, P>(x, buf, t, bar);
+            else exchange<LOG2N, P + 1, P>(x, buf, t, bar);
+            ++xc;
+        }
         if constexpr (late) tw.template fetch<LOG2N, P>(f, t);
         tw.template apply<true>(x, f);
     }

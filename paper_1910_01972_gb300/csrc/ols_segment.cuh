@@ -17,7 +17,7 @@ namespace ols {
 // (32 columns) instead of registers; implied by TMEM twiddles (columns 96..127).
 // BAR: the barrier of the segment's exchanges (the whole CTA by default, or
 // only the segment's own threads).
-template <int LOG2N, class TW, bool XT = std::is_same<TW, TwTmem>::value, class BAR = CtaBarrier>
+template <int LOG2N, class TW, bool XT = is_tw_tmem<TW>::value, class BAR = CtaBarrier>
 __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long long Ns,
                                             const float4 *__restrict__ Hk, const TW &tw,
                                             float2 *__restrict__ y, int M, int F, long long L,
@@ -41,7 +41,7 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
     constexpr bool x_in_tmem = XT;
     uint32_t xcol = 0;
     if constexpr (x_in_tmem) {
-        if constexpr (std::is_same<TW, TwTmem>::value) xcol = tw.base + 96;
+        if constexpr (is_tw_tmem<TW>::value) xcol = tw.base + 96;
         else xcol = xcol_t;
         tmem::st32(xcol, reinterpret_cast<const float *>(X));
         tmem::wait_st();

@@ -1,5 +1,5 @@
 // tmem.cuh -- Tensor Memory (TMEM) as per-thread storage: allocation and
-// 32-column loads/stores through inline PTX (tcgen05, sm_100+ family).
+// loads/stores through inline PTX (tcgen05, sm_100+ family).
 //
 // TMEM is 128 lanes x 512 columns of 32-bit cells per SM.  A warp may only
 // touch the 32-lane quarter (warp id mod 4); with the 32x32b shape thread i
@@ -68,6 +68,41 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
                    "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),
                    "=f"(v[15])
                  : "r"(taddr)
+                 : "memory");
+}
+
+// The 16-lane shapes (lane field of taddr: quarter base, or base + 16).
+// 16x256b: thread T's register i = 4 r + 2 j + e sits at lane 8 j + T / 4,
+// column 8 r + 2 (T mod 4) + e; four repetitions (.x4) span 32 columns.
+__device__ __forceinline__ void st16x256b_x4(uint32_t taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.16x256b.x4.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16};" ::"r"(taddr),
+                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+                 "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+                 : "memory");
+}
+__device__ __forceinline__ void ld16x256b_x4(uint32_t taddr, float *v) {
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),
+                   "=f"(v[15])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// 16x32bx2 with half offset OFF: thread T's register r sits at lane T mod 16,
+// column r + OFF (T / 16).
+template <int OFF>
+__device__ __forceinline__ void st16x32bx2_x4(uint32_t taddr, float a, float b, float c, float d) {
+    asm volatile("tcgen05.st.sync.aligned.16x32bx2.x4.b32 [%0], %1, {%2,%3,%4,%5};" ::"r"(taddr), "n"(OFF), "f"(a),
+                 "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+template <int OFF>
+__device__ __forceinline__ void ld16x32bx2_x4(uint32_t taddr, float &a, float &b, float &c, float &d) {
+    asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x4.b32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
+                 : "r"(taddr), "n"(OFF)
                  : "memory");
 }
 
