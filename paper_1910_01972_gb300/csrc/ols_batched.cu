@@ -36,8 +36,9 @@ ols_batched_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__rest
     tmem::fence_before_sync();
     __syncthreads();
     tmem::fence_after_sync();
-    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-    tw_tmem_fill<LOG2N>(twg, tw.base, t);
+    // the TMEM exchange except at N = 1024 (slower there in the batch: 9.10 vs 8.87 ms)
+    const TwTmemT<LOG2N != 10> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N, LOG2N != 10>(twg, tw.base, t);
 #else
     (void)tbase;
     const TwGlobal tw{twg};
@@ -143,9 +144,11 @@ __device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int til
 #if OLS_FWD_TW_TMEM
         // the same TMEM layout as the plain kernel (twiddles of this N, then the
         // segment spectrum), so results stay bitwise those of per-problem calls
-        const TwTmem twt{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-        tw_tmem_fill<LOG2N>(tw, twt.base, t);
-        ols_segment<LOG2N, TwTmem, true, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, twt, y_ptrs[P.index],
+        // (the TMEM exchange except at N = 1024: slower there in the batch, 9.10 vs 8.87 ms)
+        using TWT = TwTmemT<LOG2N != 10>;
+        const TWT twt{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+        tw_tmem_fill<LOG2N, LOG2N != 10>(tw, twt.base, t);
+        ols_segment<LOG2N, TWT, true, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, twt, y_ptrs[P.index],
                                                                P.M, P.F, P.L, P.Nout, seg, seg < P.nseg, bufs, t, xc,
                                                                0u, bar);
 #else

@@ -47,7 +47,10 @@
 #define OLS_FWD_X_TMEM 0     // 1: the forward kernel keeps only the segment spectrum in TMEM
 #endif
 #ifndef OLS_TMEM_XCHG
-#define OLS_TMEM_XCHG 1      // N = 2048 segments exchange between their last two passes through TMEM (0: shared memory)
+#define OLS_TMEM_XCHG 1      // N = 1024 and 2048: the exchange between the last two passes goes through TMEM (0: shared memory)
+#endif
+#ifndef OLS_TX10
+#define OLS_TX10 1
 #endif
 #ifndef OLS_WARPS_PER_SM
 #define OLS_WARPS_PER_SM 16  // resident warps per SM the register budget must allow
@@ -75,7 +78,9 @@ struct Geo {
     static constexpr int TWN = tw_off(NP - 1);
     // the exchange between the last two passes goes through TMEM (kernels
     // with TMEM twiddles; columns 64..95 of the thread's block are free)
-    static constexpr bool TX = OLS_TMEM_XCHG && OLS_FWD_TW_TMEM && LOG2N == 11;
+    static constexpr bool TX = OLS_TMEM_XCHG && OLS_FWD_TW_TMEM && ((LOG2N == 10 && OLS_TX10) || LOG2N == 11);
+    // ... with pass NP-2's lanes relabelled (N = 2048)
+    static constexpr bool TX_RELABEL = TX && LOG2N == 11;
     static constexpr int TWN_PAD = OLS_TW_GLOBAL ? 0 : ((TWN + 1) & ~1);   // keep buffers 16-byte aligned
     static constexpr int XBUFS = OLS_XBUFS;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * XBUFS * PADN);
@@ -244,12 +249,78 @@ __device__ __forceinline__ void tx11_inverse(float2 *x, uint32_t xb) {
     tmem::wait_ld();
 }
 
+// N = 1024 (Geo<10>::TX): pass 1 (radix 16 over p2..p5) has thread lanes
+// (p0, p1, p6, p7, p8), warp p9; pass 2 (radix 4 over p0, p1) thread = p4..p9,
+// register = p0..p3.  One round trip, pass 1 -> pass 2: 16x256b stores
+// (lane = (p6, p7, p8, p4, p3), column = (p5, p0, p1, re/im, p2)) then
+// 16x64b loads; no relabelling, so the shared exchange and twiddles of the
+// other passes are the plain ones.
+__device__ __forceinline__ void tx10_forward(float2 *x, uint32_t xb) {
+#pragma unroll
+    for (int p3 = 0; p3 < 2; ++p3) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {   // i = p5 + 2 p4 + 4 (re/im + 2 p2)
+            const int p5 = i & 1, p4 = (i >> 1) & 1, e = (i >> 2) & 1, p2 = i >> 3;
+            const float2 u = x[p2 + 2 * p3 + 4 * p4 + 8 * p5];
+            v[i] = e ? u.y : u.x;
+        }
+        tmem::st16x256b_x4(xb + ((uint32_t)p3 << 20), v);
+    }
+    tmem::wait_st();
+    __syncwarp();
+    float w[2][16];
+    tmem::ld16x64b_x16(xb, w[0]);
+    tmem::ld16x64b_x16(xb + (16u << 16), w[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {   // k = p0 + 2 p1 + 4 p2 + 8 p3
+        const int p01 = k & 3, p2 = (k >> 2) & 1, p3 = k >> 3;
+        x[k] = make_float2(w[p3][p01 + 8 * p2], w[p3][p01 + 4 + 8 * p2]);
+    }
+}
+__device__ __forceinline__ void tx10_inverse(float2 *x, uint32_t xb) {
+    float w[2][16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int p01 = k & 3, p2 = (k >> 2) & 1, p3 = k >> 3;
+        w[p3][p01 + 8 * p2] = x[k].x;
+        w[p3][p01 + 4 + 8 * p2] = x[k].y;
+    }
+    tmem::st16x64b_x16(xb, w[0]);
+    tmem::st16x64b_x16(xb + (16u << 16), w[1]);
+    tmem::wait_st();
+    __syncwarp();
+    float v[2][16];
+    tmem::ld16x256b_x4(xb, v[0]);
+    tmem::ld16x256b_x4(xb + (16u << 16), v[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int p3 = 0; p3 < 2; ++p3)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {   // re at i = p5 + 2 p4 + 8 p2, im at i + 4
+            const int p5 = m & 1, p4 = (m >> 1) & 1, p2 = m >> 2, i = p5 + 2 * p4 + 8 * p2;
+            x[p2 + 2 * p3 + 4 * p4 + 8 * p5] = make_float2(v[p3][i], v[p3][i + 4]);
+        }
+}
+
+template <int LOG2N>
+__device__ __forceinline__ void tx_forward(float2 *x, uint32_t xb) {
+    if constexpr (LOG2N == 11) tx11_forward(x, xb);
+    else tx10_forward(x, xb);
+}
+template <int LOG2N>
+__device__ __forceinline__ void tx_inverse(float2 *x, uint32_t xb) {
+    if constexpr (LOG2N == 11) tx11_inverse(x, xb);
+    else tx10_inverse(x, xb);
+}
+
 // Index n' = position mod s of pass P's twiddle W_{16 s}^{n' k} for thread t
 // (XCH: the kernel uses the TMEM exchange, which relabels pass NP-2).
 template <int LOG2N, int P, bool XCH>
 __device__ __forceinline__ int tw_index(int t) {
     using G = Geo<LOG2N>;
-    if constexpr (XCH && G::TX && P == G::NP - 2) return (t >> 1) & 7;   // lanes 1..3 hold p0..p2
+    if constexpr (XCH && G::TX_RELABEL && P == G::NP - 2) return (t >> 1) & 7;   // lanes 1..3 hold p0..p2
     else return t % G::stride(P);
 }
 
@@ -391,10 +462,10 @@ __device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const TW
         tw.template apply<false>(x, f);
         constexpr bool tx = G::TX && tw_xchg<TW>();
         if constexpr (tx && P == G::NP - 2) {
-            tx11_forward(x, tw.xbase());
+            tx_forward<LOG2N>(x, tw.xbase());
         } else {
             float2 *buf = bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0);
-            if constexpr (tx && P + 1 == G::NP - 2) exchange_tx11<P, P + 1>(x, buf, t, bar);
+            if constexpr (tx && G::TX_RELABEL && P + 1 == G::NP - 2) exchange_tx11<P, P + 1>(x, buf, t, bar);
             else exchange<LOG2N, P, P + 1>(x, buf, t, bar);
             ++xc;
         }
@@ -423,10 +494,10 @@ __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const TW
         constexpr bool late = (OLS_TW_TMEM_LATE || (tx && P == G::NP - 2)) && is_tw_tmem<TW>::value;
         if constexpr (!late) tw.template fetch<LOG2N, P>(f, t);
         if constexpr (tx && P == G::NP - 2) {
-            tx11_inverse(x, tw.xbase());
+            tx_inverse<LOG2N>(x, tw.xbase());
         } else {
             float2 *buf = bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0);
-            if constexpr (tx && P + 1 == G::NP - 2) exchange_tx11<P + 1, P>(x, buf, t, bar);
+            if constexpr (tx && G::TX_RELABEL && P + 1 == G::NP - 2) exchange_tx11<P + 1, P>(x, buf, t, bar);
             else exchange<LOG2N, P + 1, P>(x, buf, t, bar);
             ++xc;
         }

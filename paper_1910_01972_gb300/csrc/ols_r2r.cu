@@ -67,8 +67,10 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
     tmem::fence_before_sync();
     __syncthreads();
     tmem::fence_after_sync();
-    const TwTmem tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-    tw_tmem_fill<LOG2N>(twg, tw.base, t);
+    // the TMEM exchange at N = 2048 only (at N = 1024 this kernel spills with it)
+    constexpr bool xch = LOG2N != 10;
+    const TwTmemT<xch> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N, xch>(twg, tw.base, t);
     const uint32_t xcol = tw.base + 96;
 #else
     (void)tbase;

@@ -52,47 +52,40 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
     const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
     const long long obase = start - lo;
 
-#if OLS_PREFETCH_H
+    // N = 1024 with the TMEM exchange runs without the spectrum prefetch: its
+    // 32 registers make that kernel spill (0.153 ms without, 0.166 ms with)
+    constexpr bool prefetch = OLS_PREFETCH_H && !(G::TX && tw_xchg<TW>() && LOG2N == 10);
     float4 hn[8];
+    if constexpr (prefetch) {
 #pragma unroll
-    for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
-#endif
+        for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
+    }
     for (int f = 0; f < F; ++f) {
         float2 x[16];
-#if OLS_PREFETCH_H
         if constexpr (x_in_tmem) {
             tmem::ld32(xcol, reinterpret_cast<float *>(x));
             tmem::wait_ld();
         } else {
 #pragma unroll
             for (int j = 0; j < 16; ++j) x[j] = X[j];
+        }
+        if constexpr (!prefetch) {
+            const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
         }
 #pragma unroll
         for (int j2 = 0; j2 < 8; ++j2) {
             x[2 * j2] = cmul(x[2 * j2], make_float2(hn[j2].x, hn[j2].y));
             x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(hn[j2].z, hn[j2].w));
         }
-        if (f + 1 < F) {
-            const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
+        if constexpr (prefetch) {
+            if (f + 1 < F) {
+                const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
 #pragma unroll
-            for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+                for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+            }
         }
-#else
-        const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
-        if constexpr (x_in_tmem) {
-            tmem::ld32(xcol, reinterpret_cast<float *>(x));
-            tmem::wait_ld();
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) x[j] = X[j];
-        }
-#pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2) {
-            const float4 h = load_spectrum(hp + j2 * G::T);
-            x[2 * j2] = cmul(x[2 * j2], make_float2(h.x, h.y));
-            x[2 * j2 + 1] = cmul(x[2 * j2 + 1], make_float2(h.z, h.w));
-        }
-#endif
         inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc, bar);
         float2 *dst = y + (size_t)f * (size_t)Nout;
 #pragma unroll
