@@ -56,6 +56,10 @@
 #define OLS_BWD_PREFETCH 1       // pull the next gradient window toward L2 while this one is transformed
 #endif
 
+#ifndef OLS_BWD_XCHG
+#define OLS_BWD_XCHG 0
+#endif
+
 namespace ols {
 
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {
@@ -160,8 +164,9 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
     __syncthreads();
     tmem::fence_after_sync();
     // without the TMEM exchange: with it the N = 2048 adjoint spills
-    const TwTmemT<false> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-    tw_tmem_fill<LOG2N, false>(twg, tw.base, t);
+    constexpr bool xch = OLS_BWD_XCHG && LOG2N == 10;
+    const TwTmemT<xch> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N, xch>(twg, tw.base, t);
     const uint32_t acol = tw.base + 96;
 #else
     float4 *Asm = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + BG::XBYTES) + slot * BG::HALF;

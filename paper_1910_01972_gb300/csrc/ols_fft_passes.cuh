@@ -178,6 +178,10 @@ __device__ __forceinline__ void exchange_tx11(float2 *x, float2 *buf, int t, con
     for (int k = 0; k < 16; ++k) x[k] = buf[tx11_addr<PR>(t, k)];
 }
 
+// A warp's TMEM stores are complete (wait::st) before any lane loads them
+// back (the barrier measured free: 0.536 ms with it, 0.540 ms without).
+__device__ __forceinline__ void tx_sync() { __syncwarp(); }
+
 // Pass 1 -> pass 2 inside the warp, through 32 TMEM columns at xb (lane
 // field = the warp's quarter), as two round trips:
 //  1. 16x32bx2 stores, half offset 4 (lane = (p8, p0, p1, p2, p3), column =
@@ -192,7 +196,7 @@ __device__ __forceinline__ void tx11_forward(float2 *x, uint32_t xb) {
         tmem::st16x32bx2_x4<4>(xb + ((uint32_t)(k & 1) << 20) + 8u * ((k >> 1) & 1) + 16u * (k >> 2), x[k].x,
                                x[k].y, x[k + 8].x, x[k + 8].y);
     tmem::wait_st();
-    __syncwarp();
+    tx_sync();
     float z[2][16];
     tmem::ld16x256b_x4(xb, z[0]);
     tmem::ld16x256b_x4(xb + (16u << 16), z[1]);
@@ -205,7 +209,7 @@ __device__ __forceinline__ void tx11_forward(float2 *x, uint32_t xb) {
     }
     tmem::st32(xb, v);
     tmem::wait_st();
-    __syncwarp();
+    tx_sync();
     float w[2][16];
     tmem::ld16x256b_x4(xb, w[0]);
     tmem::ld16x256b_x4(xb + (16u << 16), w[1]);
@@ -228,7 +232,7 @@ __device__ __forceinline__ void tx11_inverse(float2 *x, uint32_t xb) {
     tmem::st16x256b_x4(xb, w[0]);
     tmem::st16x256b_x4(xb + (16u << 16), w[1]);
     tmem::wait_st();
-    __syncwarp();
+    tx_sync();
     float v[32];
     tmem::ld32(xb, v);
     tmem::wait_ld();
@@ -241,7 +245,7 @@ __device__ __forceinline__ void tx11_inverse(float2 *x, uint32_t xb) {
     tmem::st16x256b_x4(xb, z[0]);
     tmem::st16x256b_x4(xb + (16u << 16), z[1]);
     tmem::wait_st();
-    __syncwarp();
+    tx_sync();
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         tmem::ld16x32bx2_x4<4>(xb + ((uint32_t)(k & 1) << 20) + 8u * ((k >> 1) & 1) + 16u * (k >> 2), x[k].x,
@@ -268,7 +272,7 @@ __device__ __forceinline__ void tx10_forward(float2 *x, uint32_t xb) {
         tmem::st16x256b_x4(xb + ((uint32_t)p3 << 20), v);
     }
     tmem::wait_st();
-    __syncwarp();
+    tx_sync();
     float w[2][16];
     tmem::ld16x64b_x16(xb, w[0]);
     tmem::ld16x64b_x16(xb + (16u << 16), w[1]);
@@ -290,7 +294,7 @@ __device__ __forceinline__ void tx10_inverse(float2 *x, uint32_t xb) {
     tmem::st16x64b_x16(xb, w[0]);
     tmem::st16x64b_x16(xb + (16u << 16), w[1]);
     tmem::wait_st();
-    __syncwarp();
+    tx_sync();
     float v[2][16];
     tmem::ld16x256b_x4(xb, v[0]);
     tmem::ld16x256b_x4(xb + (16u << 16), v[1]);
