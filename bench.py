@@ -69,6 +69,14 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def fp32_flops(N, F, nseg):
+    """FP32 operations of one call by the conventional count: 5 N log2 N per
+    complex N-point FFT (one forward per segment, one inverse per segment and
+    filter) and 6 per complex product of a spectrum point."""
+    lg = N.bit_length() - 1
+    return nseg * (F + 1) * 5 * N * lg + nseg * F * 6 * N
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
@@ -698,6 +706,19 @@ def run_ours(args):
         others, samples = measure_others(peak)
     clk = clocks.stop()
 
+    # FP32 roofline (context beside the HBM one): the conventional operation
+    # count against the peak of the FP32 units (SMs x 128 lanes x 2 operations
+    # per FMA x the SM clock measured under load, else the maximum clock)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    flops = fp32_flops(cfg.N, cfg.F, nseg)
+    fp32_achieved = flops / (ms_step * 1e-3) / 1e12
+    roof_fp32 = {"bound": "fp32", "achieved": fp32_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "frac": fp32_achieved / fp32_peak, "flops_per_launch": flops,
+                 "count": "5 N log2 N per complex FFT + 6 per complex product",
+                 "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, mhz)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, desc, ns, y_ref = oracle_rate(s_np, h_np, args.cpu_seconds)
@@ -720,6 +741,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline_fp32": roof_fp32,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
