@@ -15,6 +15,15 @@
 #include "ols_internal.h"
 #include "ols_segment.cuh"
 
+// Segment lengths whose batch items use the TMEM exchange (bit i: N = 2^(9 + i)):
+// N = 2048 only.  The single-launch kernel holds every segment length's body,
+// so it runs at the register budget of the hungriest one: with the exchange
+// also at N = 1024 the batch took 9.10 instead of 8.87 ms, at 512 and 4096
+// 10.6-11.1 ms.
+#ifndef OLS_BATCH_TX_MASK
+#define OLS_BATCH_TX_MASK 0x4
+#endif
+
 namespace ols {
 
 template <int LOG2N>
@@ -36,9 +45,10 @@ ols_batched_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__rest
     tmem::fence_before_sync();
     __syncthreads();
     tmem::fence_after_sync();
-    // the TMEM exchange except at N = 1024 (slower there in the batch: 9.10 vs 8.87 ms)
-    const TwTmemT<LOG2N != 10> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-    tw_tmem_fill<LOG2N, LOG2N != 10>(twg, tw.base, t);
+    // the TMEM exchange at the segment lengths of OLS_BATCH_TX_MASK
+    constexpr bool xch = in_tx_mask<LOG2N>(OLS_BATCH_TX_MASK);
+    const TwTmemT<xch> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
+    tw_tmem_fill<LOG2N, xch>(twg, tw.base, t);
 #else
     (void)tbase;
     const TwGlobal tw{twg};
@@ -144,10 +154,11 @@ __device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int til
 #if OLS_FWD_TW_TMEM
         // the same TMEM layout as the plain kernel (twiddles of this N, then the
         // segment spectrum), so results stay bitwise those of per-problem calls
-        // (the TMEM exchange except at N = 1024: slower there in the batch, 9.10 vs 8.87 ms)
-        using TWT = TwTmemT<LOG2N != 10>;
+        // (the TMEM exchange at the segment lengths of OLS_BATCH_TX_MASK)
+        constexpr bool xch = in_tx_mask<LOG2N>(OLS_BATCH_TX_MASK);
+        using TWT = TwTmemT<xch>;
         const TWT twt{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-        tw_tmem_fill<LOG2N, LOG2N != 10>(tw, twt.base, t);
+        tw_tmem_fill<LOG2N, xch>(tw, twt.base, t);
         ols_segment<LOG2N, TWT, true, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, twt, y_ptrs[P.index],
                                                                P.M, P.F, P.L, P.Nout, seg, seg < P.nseg, bufs, t, xc,
                                                                0u, bar);

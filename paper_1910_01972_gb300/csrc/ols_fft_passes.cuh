@@ -47,10 +47,13 @@
 #define OLS_FWD_X_TMEM 0     // 1: the forward kernel keeps only the segment spectrum in TMEM
 #endif
 #ifndef OLS_TMEM_XCHG
-#define OLS_TMEM_XCHG 1      // N = 1024 and 2048: the exchange between the last two passes goes through TMEM (0: shared memory)
+#define OLS_TMEM_XCHG 1      // N = 512..4096: the exchange between the last two passes goes through TMEM (0: shared memory)
 #endif
-#ifndef OLS_TX10
-#define OLS_TX10 1
+#ifndef OLS_TX_MASK
+#define OLS_TX_MASK 0xF      // segment lengths with the TMEM exchange: bit i for N = 2^(9 + i)
+#endif
+#ifndef OLS_TX_NOPF_MASK
+#define OLS_TX_NOPF_MASK 0xB // ... and among them those run without the spectrum prefetch (512, 1024, 4096)
 #endif
 #ifndef OLS_WARPS_PER_SM
 #define OLS_WARPS_PER_SM 16  // resident warps per SM the register budget must allow
@@ -78,9 +81,11 @@ struct Geo {
     static constexpr int TWN = tw_off(NP - 1);
     // the exchange between the last two passes goes through TMEM (kernels
     // with TMEM twiddles; columns 64..95 of the thread's block are free)
-    static constexpr bool TX = OLS_TMEM_XCHG && OLS_FWD_TW_TMEM && ((LOG2N == 10 && OLS_TX10) || LOG2N == 11);
+    static constexpr bool TX = OLS_TMEM_XCHG && OLS_FWD_TW_TMEM && LOG2N >= 9 && LOG2N <= 12 &&
+                               ((OLS_TX_MASK >> (LOG2N - 9)) & 1);
+    static constexpr bool TX_NOPF = TX && ((OLS_TX_NOPF_MASK >> (LOG2N - 9)) & 1);
     // ... with pass NP-2's lanes relabelled (N = 2048)
-    static constexpr bool TX_RELABEL = TX && LOG2N == 11;
+    static constexpr bool TX_RELABEL = TX && LOG2N != 10;
     static constexpr int TWN_PAD = OLS_TW_GLOBAL ? 0 : ((TWN + 1) & ~1);   // keep buffers 16-byte aligned
     static constexpr int XBUFS = OLS_XBUFS;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * XBUFS * PADN);
@@ -96,6 +101,13 @@ struct Geo {
                                             ? SEGS * XBUFS * PADN * sizeof(float2)
                                             : (228u * 1024u) / (TMEM_MAX_CTAS + 1) + 1024u;
 };
+
+// Whether segment length 2^LOG2N is in a mask of segment lengths (bit i for
+// N = 2^(9 + i)), the form of the per-kernel TMEM-exchange choices.
+template <int LOG2N>
+__host__ __device__ constexpr bool in_tx_mask(unsigned mask) {
+    return LOG2N >= 9 && LOG2N <= 12 && ((mask >> (LOG2N - 9)) & 1u);
+}
 
 // Padded shared-memory base of thread t in the layout of pass P:
 // positions (t / s) * 16 s + (t % s) + k s, padded q -> q + q / 16.
@@ -163,19 +175,37 @@ __device__ __forceinline__ int tx11_addr1(int t, int k) {
     const int base = ((t >> 1) & 7) + 128 * ((t >> 4) & 1) + 256 * (t & 1) + 512 * (t >> 5);
     return base + 8 * ((k & 1) ^ (t & 1)) + 16 * (k >> 1);
 }
-template <int P>
-__device__ __forceinline__ int tx11_addr(int t, int k) {
-    if constexpr (P == 0) return tx11_addr0(t, k);
-    else return tx11_addr1(t, k);
+
+// N = 4096 (Geo<12>::TX): pass 0 thread = p0..p7, register = p8..p11; pass 1
+// (radix 16 over p4..p7) lanes (p0, p1, p8, p2, p3), warp p9..p11; pass 2
+// thread = p4..p11.  Shared exchange of passes 0 and 1: position q at
+// q + 8 (q >> 8): 16 distinct bank pairs per half warp in both layouts.
+__device__ __forceinline__ int tx12_addr0(int t, int k) { return t + 264 * k; }
+__device__ __forceinline__ int tx12_addr1(int t, int k) {
+    return (t & 3) + 4 * ((t >> 3) & 1) + 8 * ((t >> 4) & 1) + 264 * ((t >> 2) & 1) + 528 * (t >> 5) + 16 * k;
 }
-template <int PW, int PR, class BAR>
-__device__ __forceinline__ void exchange_tx11(float2 *x, float2 *buf, int t, const BAR &bar) {
-    if constexpr (Geo<11>::XBUFS == 1) bar();
+// N = 512 (Geo<9>::TX): pass 0 thread = p0..p4, register = p5..p8; pass 1
+// (radix 16 over p1..p4) lanes (p5, p0, p6, p7, p8); pass 2 thread = p4..p8.
+// Shared exchange: position q at q + 2 (q >> 5).
+__device__ __forceinline__ int tx9_addr0(int t, int k) { return t + 34 * k; }
+__device__ __forceinline__ int tx9_addr1(int t, int k) {
+    return ((t >> 1) & 1) + 34 * ((t & 1) + 2 * ((t >> 2) & 1) + 4 * ((t >> 3) & 1) + 8 * ((t >> 4) & 1)) + 2 * k;
+}
+template <int LOG2N, int P>
+__device__ __forceinline__ int tx_addr(int t, int k) {
+    if constexpr (LOG2N == 11) return P == 0 ? tx11_addr0(t, k) : tx11_addr1(t, k);
+    else if constexpr (LOG2N == 12) return P == 0 ? tx12_addr0(t, k) : tx12_addr1(t, k);
+    else return P == 0 ? tx9_addr0(t, k) : tx9_addr1(t, k);
+}
+// The shared-memory exchange of passes 0 and 1 when pass 1 is relabelled.
+template <int LOG2N, int PW, int PR, class BAR>
+__device__ __forceinline__ void exchange_tx(float2 *x, float2 *buf, int t, const BAR &bar) {
+    if constexpr (Geo<LOG2N>::XBUFS == 1) bar();
 #pragma unroll
-    for (int k = 0; k < 16; ++k) buf[tx11_addr<PW>(t, k)] = x[k];
+    for (int k = 0; k < 16; ++k) buf[tx_addr<LOG2N, PW>(t, k)] = x[k];
     bar();
 #pragma unroll
-    for (int k = 0; k < 16; ++k) x[k] = buf[tx11_addr<PR>(t, k)];
+    for (int k = 0; k < 16; ++k) x[k] = buf[tx_addr<LOG2N, PR>(t, k)];
 }
 
 // A warp's TMEM stores are complete (wait::st) before any lane loads them
@@ -308,15 +338,155 @@ __device__ __forceinline__ void tx10_inverse(float2 *x, uint32_t xb) {
         }
 }
 
+// N = 4096, pass 1 -> pass 2 (registers p4 + 2 p5 + 4 p6 + 8 p7), two round
+// trips:
+//  1. 16x256b stores (lane = (p8, p2, p3, p6, p4), column = (p7, p0, p1,
+//     re/im, p5)); 16x64b loads: thread lanes (p6, p7, p8, p2, p3), registers
+//     z[p4][p0 + 2 p1 + 4 re/im + 8 p5];
+//  2. a 32x32b store (column = (re/im, p4, p5, p0, p1)); 16x256b loads: thread
+//     lanes (p4..p8), x[p0 + 2 p1 + 4 p2 + 8 p3] from w[p3][4 (p0 + 2 p1) + 2 p2
+//     + re/im].
+__device__ __forceinline__ void tx12_forward(float2 *x, uint32_t xb) {
+#pragma unroll
+    for (int p4 = 0; p4 < 2; ++p4) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {   // i = p7 + 2 p6 + 4 (re/im + 2 p5)
+            const int p7 = i & 1, p6 = (i >> 1) & 1, e = (i >> 2) & 1, p5 = i >> 3;
+            const float2 u = x[p4 + 2 * p5 + 4 * p6 + 8 * p7];
+            v[i] = e ? u.y : u.x;
+        }
+        tmem::st16x256b_x4(xb + ((uint32_t)p4 << 20), v);
+    }
+    tmem::wait_st();
+    tx_sync();
+    float z[2][16];
+    tmem::ld16x64b_x16(xb, z[0]);
+    tmem::ld16x64b_x16(xb + (16u << 16), z[1]);
+    tmem::wait_ld();
+    float v[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {   // m = re/im + 2 p4 + 4 p5 + 8 p0 + 16 p1 (the column)
+        const int e = m & 1, p4 = (m >> 1) & 1, p5 = (m >> 2) & 1, p0 = (m >> 3) & 1, p1 = m >> 4;
+        v[m] = z[p4][p0 + 2 * p1 + 4 * e + 8 * p5];
+    }
+    tmem::st32(xb, v);
+    tmem::wait_st();
+    tx_sync();
+    float w[2][16];
+    tmem::ld16x256b_x4(xb, w[0]);
+    tmem::ld16x256b_x4(xb + (16u << 16), w[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {   // k = p0 + 2 p1 + 4 p2 + 8 p3
+        const int p01 = k & 3, p2 = (k >> 2) & 1, p3 = k >> 3;
+        x[k] = make_float2(w[p3][4 * p01 + 2 * p2], w[p3][4 * p01 + 2 * p2 + 1]);
+    }
+}
+__device__ __forceinline__ void tx12_inverse(float2 *x, uint32_t xb) {
+    float w[2][16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int p01 = k & 3, p2 = (k >> 2) & 1, p3 = k >> 3;
+        w[p3][4 * p01 + 2 * p2] = x[k].x;
+        w[p3][4 * p01 + 2 * p2 + 1] = x[k].y;
+    }
+    tmem::st16x256b_x4(xb, w[0]);
+    tmem::st16x256b_x4(xb + (16u << 16), w[1]);
+    tmem::wait_st();
+    tx_sync();
+    float v[32];
+    tmem::ld32(xb, v);
+    tmem::wait_ld();
+    float z[2][16];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const int e = m & 1, p4 = (m >> 1) & 1, p5 = (m >> 2) & 1, p0 = (m >> 3) & 1, p1 = m >> 4;
+        z[p4][p0 + 2 * p1 + 4 * e + 8 * p5] = v[m];
+    }
+    tmem::st16x64b_x16(xb, z[0]);
+    tmem::st16x64b_x16(xb + (16u << 16), z[1]);
+    tmem::wait_st();
+    tx_sync();
+    float u[2][16];
+    tmem::ld16x256b_x4(xb, u[0]);
+    tmem::ld16x256b_x4(xb + (16u << 16), u[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int p4 = 0; p4 < 2; ++p4)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {   // re at i = p7 + 2 p6 + 8 p5, im at i + 4
+            const int p7 = m & 1, p6 = (m >> 1) & 1, p5 = m >> 2, i = p7 + 2 * p6 + 8 * p5;
+            x[p4 + 2 * p5 + 4 * p6 + 8 * p7] = make_float2(u[p4][i], u[p4][i + 4]);
+        }
+}
+
+// N = 512, pass 1 -> pass 2 (registers p1 + 2 p2 + 4 p3 + 8 p4), one round
+// trip: 16x256b stores (lane = (p6, p7, p8, p1, p2), column = (p4, p5, p0,
+// re/im, p3)); 16x128b loads: thread lanes (p4..p8), x[p0 + 2 p1 + 4 p2 + 8 p3]
+// from w[p2][2 (p0 + 2 re/im + 4 p3) + p1].
+__device__ __forceinline__ void tx9_forward(float2 *x, uint32_t xb) {
+#pragma unroll
+    for (int p2 = 0; p2 < 2; ++p2) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {   // i = p4 + 2 p1 + 4 (re/im + 2 p3)
+            const int p4 = i & 1, p1 = (i >> 1) & 1, e = (i >> 2) & 1, p3 = i >> 3;
+            const float2 u = x[p1 + 2 * p2 + 4 * p3 + 8 * p4];
+            v[i] = e ? u.y : u.x;
+        }
+        tmem::st16x256b_x4(xb + ((uint32_t)p2 << 20), v);
+    }
+    tmem::wait_st();
+    tx_sync();
+    float w[2][16];
+    tmem::ld16x128b_x8(xb, w[0]);
+    tmem::ld16x128b_x8(xb + (16u << 16), w[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {   // k = p0 + 2 p1 + 4 p2 + 8 p3
+        const int p0 = k & 1, p1 = (k >> 1) & 1, p2 = (k >> 2) & 1, p3 = k >> 3;
+        x[k] = make_float2(w[p2][2 * (p0 + 4 * p3) + p1], w[p2][2 * (p0 + 2 + 4 * p3) + p1]);
+    }
+}
+__device__ __forceinline__ void tx9_inverse(float2 *x, uint32_t xb) {
+    float w[2][16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int p0 = k & 1, p1 = (k >> 1) & 1, p2 = (k >> 2) & 1, p3 = k >> 3;
+        w[p2][2 * (p0 + 4 * p3) + p1] = x[k].x;
+        w[p2][2 * (p0 + 2 + 4 * p3) + p1] = x[k].y;
+    }
+    tmem::st16x128b_x8(xb, w[0]);
+    tmem::st16x128b_x8(xb + (16u << 16), w[1]);
+    tmem::wait_st();
+    tx_sync();
+    float v[2][16];
+    tmem::ld16x256b_x4(xb, v[0]);
+    tmem::ld16x256b_x4(xb + (16u << 16), v[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int p2 = 0; p2 < 2; ++p2)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {   // re at i = p4 + 2 p1 + 8 p3, im at i + 4
+            const int p4 = m & 1, p1 = (m >> 1) & 1, p3 = m >> 2, i = p4 + 2 * p1 + 8 * p3;
+            x[p1 + 2 * p2 + 4 * p3 + 8 * p4] = make_float2(v[p2][i], v[p2][i + 4]);
+        }
+}
+
 template <int LOG2N>
 __device__ __forceinline__ void tx_forward(float2 *x, uint32_t xb) {
-    if constexpr (LOG2N == 11) tx11_forward(x, xb);
-    else tx10_forward(x, xb);
+    if constexpr (LOG2N == 12) tx12_forward(x, xb);
+    else if constexpr (LOG2N == 11) tx11_forward(x, xb);
+    else if constexpr (LOG2N == 10) tx10_forward(x, xb);
+    else tx9_forward(x, xb);
 }
 template <int LOG2N>
 __device__ __forceinline__ void tx_inverse(float2 *x, uint32_t xb) {
-    if constexpr (LOG2N == 11) tx11_inverse(x, xb);
-    else tx10_inverse(x, xb);
+    if constexpr (LOG2N == 12) tx12_inverse(x, xb);
+    else if constexpr (LOG2N == 11) tx11_inverse(x, xb);
+    else if constexpr (LOG2N == 10) tx10_inverse(x, xb);
+    else tx9_inverse(x, xb);
 }
 
 // Index n' = position mod s of pass P's twiddle W_{16 s}^{n' k} for thread t
@@ -324,7 +494,11 @@ __device__ __forceinline__ void tx_inverse(float2 *x, uint32_t xb) {
 template <int LOG2N, int P, bool XCH>
 __device__ __forceinline__ int tw_index(int t) {
     using G = Geo<LOG2N>;
-    if constexpr (XCH && G::TX_RELABEL && P == G::NP - 2) return (t >> 1) & 7;   // lanes 1..3 hold p0..p2
+    if constexpr (XCH && G::TX_RELABEL && P == G::NP - 2) {   // the relabelled lanes holding p0 .. p(s-1)
+        if constexpr (LOG2N == 11) return (t >> 1) & 7;
+        else if constexpr (LOG2N == 12) return (t & 3) + 4 * ((t >> 3) & 1) + 8 * ((t >> 4) & 1);
+        else return (t >> 1) & 1;
+    }
     else return t % G::stride(P);
 }
 
@@ -469,7 +643,7 @@ __device__ __forceinline__ void forward_passes(float2 *x, float2 *bufs, const TW
             tx_forward<LOG2N>(x, tw.xbase());
         } else {
             float2 *buf = bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0);
-            if constexpr (tx && G::TX_RELABEL && P + 1 == G::NP - 2) exchange_tx11<P, P + 1>(x, buf, t, bar);
+            if constexpr (tx && G::TX_RELABEL && P + 1 == G::NP - 2) exchange_tx<LOG2N, P, P + 1>(x, buf, t, bar);
             else exchange<LOG2N, P, P + 1>(x, buf, t, bar);
             ++xc;
         }
@@ -501,7 +675,7 @@ __device__ __forceinline__ void inverse_passes(float2 *x, float2 *bufs, const TW
             tx_inverse<LOG2N>(x, tw.xbase());
         } else {
             float2 *buf = bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0);
-            if constexpr (tx && G::TX_RELABEL && P + 1 == G::NP - 2) exchange_tx11<P + 1, P>(x, buf, t, bar);
+            if constexpr (tx && G::TX_RELABEL && P + 1 == G::NP - 2) exchange_tx<LOG2N, P + 1, P>(x, buf, t, bar);
             else exchange<LOG2N, P + 1, P>(x, buf, t, bar);
             ++xc;
         }

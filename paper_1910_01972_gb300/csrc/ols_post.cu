@@ -57,11 +57,11 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
     tmem::fence_before_sync();
     __syncthreads();
     tmem::fence_after_sync();
-    // the derivative runs the TMEM exchange (not at N = 1024, where it
+    // the derivative runs the TMEM exchange at N = 2048 (at other N it
     // spills); power and detection keep the exchange in shared memory (with
     // it their epilogues spill: 0.525 vs 0.535 ms and 0.582 vs 0.613 ms on
     // the filter bank)
-    constexpr bool xch = MODE == POST_DERIV && LOG2N != 10;
+    constexpr bool xch = MODE == POST_DERIV && LOG2N == 11;
     const TwTmemT<xch> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
     tw_tmem_fill<LOG2N, xch>(twg, tw.base, t);
     const uint32_t xcol = tw.base + 96;

@@ -67,8 +67,8 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
     tmem::fence_before_sync();
     __syncthreads();
     tmem::fence_after_sync();
-    // the TMEM exchange at N = 2048 only (at N = 1024 this kernel spills with it)
-    constexpr bool xch = LOG2N != 10;
+    // the TMEM exchange at N = 2048 only (at other N this kernel spills with it)
+    constexpr bool xch = LOG2N == 11;
     const TwTmemT<xch> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
     tw_tmem_fill<LOG2N, xch>(twg, tw.base, t);
     const uint32_t xcol = tw.base + 96;

@@ -52,9 +52,11 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
     const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
     const long long obase = start - lo;
 
-    // N = 1024 with the TMEM exchange runs without the spectrum prefetch: its
-    // 32 registers make that kernel spill (0.153 ms without, 0.166 ms with)
-    constexpr bool prefetch = OLS_PREFETCH_H && !(G::TX && tw_xchg<TW>() && LOG2N == 10);
+    // segment lengths in Geo<>::TX_NOPF run the TMEM exchange without the
+    // spectrum prefetch: its 32 registers make them spill (filter banks of 32
+    // filters, Ns = 2^23: N = 512 0.479 against 0.531 ms, N = 1024 0.153
+    // against 0.166 ms at Ns = 2^22, N = 4096 0.664 against 0.714 ms)
+    constexpr bool prefetch = OLS_PREFETCH_H && !(G::TX_NOPF && tw_xchg<TW>());
     float4 hn[8];
     if constexpr (prefetch) {
 #pragma unroll

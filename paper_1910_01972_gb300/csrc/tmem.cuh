@@ -90,6 +90,24 @@ __device__ __forceinline__ void ld16x256b_x4(uint32_t taddr, float *v) {
                  : "memory");
 }
 
+// 16x128b: thread T's register 2 r + j sits at lane 8 j + T / 4, column
+// 4 r + T mod 4; eight repetitions (.x8) span 32 columns.
+__device__ __forceinline__ void st16x128b_x8(uint32_t taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.16x128b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16};" ::"r"(taddr),
+                 "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+                 "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+                 : "memory");
+}
+__device__ __forceinline__ void ld16x128b_x8(uint32_t taddr, float *v) {
+    asm volatile("tcgen05.ld.sync.aligned.16x128b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),
+                   "=f"(v[15])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 // 16x64b: thread T's register r sits at lane 8 (T mod 2) + T / 4, column
 // 2 r + (T / 2 mod 2); sixteen repetitions (.x16) span 32 columns.
 __device__ __forceinline__ void st16x64b_x16(uint32_t taddr, const float *v) {
