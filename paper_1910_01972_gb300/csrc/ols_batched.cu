@@ -23,6 +23,11 @@
 #ifndef OLS_BATCH_TX_MASK
 #define OLS_BATCH_TX_MASK 0x4
 #endif
+// ... and for the kernels of the per-segment-length mode (one segment length
+// each): N = 2048 only as well (at every length: 8.90 against 8.86 ms)
+#ifndef OLS_BATCH_PERN_TX_MASK
+#define OLS_BATCH_PERN_TX_MASK 0x4
+#endif
 
 namespace ols {
 
@@ -45,8 +50,8 @@ ols_batched_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__rest
     tmem::fence_before_sync();
     __syncthreads();
     tmem::fence_after_sync();
-    // the TMEM exchange at the segment lengths of OLS_BATCH_TX_MASK
-    constexpr bool xch = in_tx_mask<LOG2N>(OLS_BATCH_TX_MASK);
+    // the TMEM exchange at the segment lengths of OLS_BATCH_PERN_TX_MASK
+    constexpr bool xch = in_tx_mask<LOG2N>(OLS_BATCH_PERN_TX_MASK);
     const TwTmemT<xch> tw{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
     tw_tmem_fill<LOG2N, xch>(twg, tw.base, t);
 #else
