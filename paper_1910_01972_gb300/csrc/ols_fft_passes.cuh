@@ -85,7 +85,7 @@ struct Geo {
                                ((OLS_TX_MASK >> (LOG2N - 9)) & 1);
     static constexpr bool TX_NOPF = TX && ((OLS_TX_NOPF_MASK >> (LOG2N - 9)) & 1);
     // ... with pass NP-2's lanes relabelled (N = 2048)
-    static constexpr bool TX_RELABEL = TX && LOG2N != 10;
+    static constexpr bool TX_RELABEL = TX;
     static constexpr int TWN_PAD = OLS_TW_GLOBAL ? 0 : ((TWN + 1) & ~1);   // keep buffers 16-byte aligned
     static constexpr int XBUFS = OLS_XBUFS;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)(TWN_PAD + SEGS * XBUFS * PADN);
@@ -191,9 +191,17 @@ __device__ __forceinline__ int tx9_addr0(int t, int k) { return t + 34 * k; }
 __device__ __forceinline__ int tx9_addr1(int t, int k) {
     return ((t >> 1) & 1) + 34 * ((t & 1) + 2 * ((t >> 2) & 1) + 4 * ((t >> 3) & 1) + 8 * ((t >> 4) & 1)) + 2 * k;
 }
+// N = 1024 (Geo<10>::TX): pass 0 thread = p0..p5, register = p6..p9; pass 1
+// (radix 16 over p2..p5) lanes (p6, p7, p8, p0, p1), warp p9; pass 2 (radix 4
+// over p0, p1) thread = p4..p9.  Shared exchange: position q at q + 2 (q >> 6).
+__device__ __forceinline__ int tx10_addr0(int t, int k) { return t + 66 * k; }
+__device__ __forceinline__ int tx10_addr1(int t, int k) {
+    return ((t >> 3) & 3) + 66 * ((t & 7) + 8 * (t >> 5)) + 4 * k;
+}
 template <int LOG2N, int P>
 __device__ __forceinline__ int tx_addr(int t, int k) {
-    if constexpr (LOG2N == 11) return P == 0 ? tx11_addr0(t, k) : tx11_addr1(t, k);
+    if constexpr (LOG2N == 10) return P == 0 ? tx10_addr0(t, k) : tx10_addr1(t, k);
+    else if constexpr (LOG2N == 11) return P == 0 ? tx11_addr0(t, k) : tx11_addr1(t, k);
     else if constexpr (LOG2N == 12) return P == 0 ? tx12_addr0(t, k) : tx12_addr1(t, k);
     else return P == 0 ? tx9_addr0(t, k) : tx9_addr1(t, k);
 }
@@ -281,61 +289,6 @@ __device__ __forceinline__ void tx11_inverse(float2 *x, uint32_t xb) {
         tmem::ld16x32bx2_x4<4>(xb + ((uint32_t)(k & 1) << 20) + 8u * ((k >> 1) & 1) + 16u * (k >> 2), x[k].x,
                                x[k].y, x[k + 8].x, x[k + 8].y);
     tmem::wait_ld();
-}
-
-// N = 1024 (Geo<10>::TX): pass 1 (radix 16 over p2..p5) has thread lanes
-// (p0, p1, p6, p7, p8), warp p9; pass 2 (radix 4 over p0, p1) thread = p4..p9,
-// register = p0..p3.  One round trip, pass 1 -> pass 2: 16x256b stores
-// (lane = (p6, p7, p8, p4, p3), column = (p5, p0, p1, re/im, p2)) then
-// 16x64b loads; no relabelling, so the shared exchange and twiddles of the
-// other passes are the plain ones.
-__device__ __forceinline__ void tx10_forward(float2 *x, uint32_t xb) {
-#pragma unroll
-    for (int p3 = 0; p3 < 2; ++p3) {
-        float v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {   // i = p5 + 2 p4 + 4 (re/im + 2 p2)
-            const int p5 = i & 1, p4 = (i >> 1) & 1, e = (i >> 2) & 1, p2 = i >> 3;
-            const float2 u = x[p2 + 2 * p3 + 4 * p4 + 8 * p5];
-            v[i] = e ? u.y : u.x;
-        }
-        tmem::st16x256b_x4(xb + ((uint32_t)p3 << 20), v);
-    }
-    tmem::wait_st();
-    tx_sync();
-    float w[2][16];
-    tmem::ld16x64b_x16(xb, w[0]);
-    tmem::ld16x64b_x16(xb + (16u << 16), w[1]);
-    tmem::wait_ld();
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {   // k = p0 + 2 p1 + 4 p2 + 8 p3
-        const int p01 = k & 3, p2 = (k >> 2) & 1, p3 = k >> 3;
-        x[k] = make_float2(w[p3][p01 + 8 * p2], w[p3][p01 + 4 + 8 * p2]);
-    }
-}
-__device__ __forceinline__ void tx10_inverse(float2 *x, uint32_t xb) {
-    float w[2][16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int p01 = k & 3, p2 = (k >> 2) & 1, p3 = k >> 3;
-        w[p3][p01 + 8 * p2] = x[k].x;
-        w[p3][p01 + 4 + 8 * p2] = x[k].y;
-    }
-    tmem::st16x64b_x16(xb, w[0]);
-    tmem::st16x64b_x16(xb + (16u << 16), w[1]);
-    tmem::wait_st();
-    tx_sync();
-    float v[2][16];
-    tmem::ld16x256b_x4(xb, v[0]);
-    tmem::ld16x256b_x4(xb + (16u << 16), v[1]);
-    tmem::wait_ld();
-#pragma unroll
-    for (int p3 = 0; p3 < 2; ++p3)
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {   // re at i = p5 + 2 p4 + 8 p2, im at i + 4
-            const int p5 = m & 1, p4 = (m >> 1) & 1, p2 = m >> 2, i = p5 + 2 * p4 + 8 * p2;
-            x[p2 + 2 * p3 + 4 * p4 + 8 * p5] = make_float2(v[p3][i], v[p3][i + 4]);
-        }
 }
 
 // N = 4096, pass 1 -> pass 2 (registers p4 + 2 p5 + 4 p6 + 8 p7), two round
@@ -474,6 +427,56 @@ __device__ __forceinline__ void tx9_inverse(float2 *x, uint32_t xb) {
         }
 }
 
+// N = 1024, pass 1 (lanes (p6, p7, p8, p0, p1), registers p2 + 2 p3 + 4 p4 +
+// 8 p5) -> pass 2 in one round trip that keeps re and im of a point in
+// adjacent registers on both sides (no register moves; a form with the plain
+// pass-1 layout, 16x256b store and 16x64b load, split them: 0.501 vs 0.493
+// ms): a 32x32b store (column = (re/im, p4, p5,
+// p2, p3)), 16x256b loads: x[p0 + 2 p1 + 4 p2 + 8 p3] from w[p1][4 (p2 + 2 p3) +
+// 2 p0 + re/im].
+__device__ __forceinline__ void tx10_forward(float2 *x, uint32_t xb) {
+    float v[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {   // m = re/im + 2 p4 + 4 p5 + 8 p2 + 16 p3 (the column)
+        const int e = m & 1, p4 = (m >> 1) & 1, p5 = (m >> 2) & 1, p2 = (m >> 3) & 1, p3 = m >> 4;
+        const float2 u = x[p2 + 2 * p3 + 4 * p4 + 8 * p5];
+        v[m] = e ? u.y : u.x;
+    }
+    tmem::st32(xb, v);
+    tmem::wait_st();
+    tx_sync();
+    float w[2][16];
+    tmem::ld16x256b_x4(xb, w[0]);
+    tmem::ld16x256b_x4(xb + (16u << 16), w[1]);
+    tmem::wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {   // k = p0 + 2 p1 + 4 p2 + 8 p3
+        const int p0 = k & 1, p1 = (k >> 1) & 1, p23 = k >> 2;
+        x[k] = make_float2(w[p1][4 * p23 + 2 * p0], w[p1][4 * p23 + 2 * p0 + 1]);
+    }
+}
+__device__ __forceinline__ void tx10_inverse(float2 *x, uint32_t xb) {
+    float w[2][16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int p0 = k & 1, p1 = (k >> 1) & 1, p23 = k >> 2;
+        w[p1][4 * p23 + 2 * p0] = x[k].x;
+        w[p1][4 * p23 + 2 * p0 + 1] = x[k].y;
+    }
+    tmem::st16x256b_x4(xb, w[0]);
+    tmem::st16x256b_x4(xb + (16u << 16), w[1]);
+    tmem::wait_st();
+    tx_sync();
+    float v[32];
+    tmem::ld32(xb, v);
+    tmem::wait_ld();
+#pragma unroll
+    for (int m = 0; m < 32; m += 2) {
+        const int p4 = (m >> 1) & 1, p5 = (m >> 2) & 1, p2 = (m >> 3) & 1, p3 = m >> 4;
+        x[p2 + 2 * p3 + 4 * p4 + 8 * p5] = make_float2(v[m], v[m + 1]);
+    }
+}
+
 template <int LOG2N>
 __device__ __forceinline__ void tx_forward(float2 *x, uint32_t xb) {
     if constexpr (LOG2N == 12) tx12_forward(x, xb);
@@ -497,6 +500,7 @@ __device__ __forceinline__ int tw_index(int t) {
     if constexpr (XCH && G::TX_RELABEL && P == G::NP - 2) {   // the relabelled lanes holding p0 .. p(s-1)
         if constexpr (LOG2N == 11) return (t >> 1) & 7;
         else if constexpr (LOG2N == 12) return (t & 3) + 4 * ((t >> 3) & 1) + 8 * ((t >> 4) & 1);
+        else if constexpr (LOG2N == 10) return (t >> 3) & 3;
         else return (t >> 1) & 1;
     }
     else return t % G::stride(P);

@@ -87,20 +87,20 @@ def test_layout_probe_facts():
 
 
 def test_n1024_one_round_trip():
-    lanes, regs = (0, 1, 6, 7, 8), (2, 3, 4, 5)      # pass 1: lanes (p0, p1, p6, p7, p8)
+    lanes, regs = (6, 7, 8, 0, 1), (2, 3, 4, 5)      # relabelled pass 1
     m = Tmem()
     for T in range(32):
-        for p3 in range(2):
-            v = [None] * 16
-            for p2, p4, p5, e in itertools.product(range(2), repeat=4):
-                v[4 * (e + 2 * p2) + 2 * p4 + p5] = (pos(lanes, regs, T, p2 + 2 * p3 + 4 * p4 + 8 * p5), e)
-            m.st(L256, T, v, lb=16 * p3)
+        v = [None] * 32
+        for mm in range(32):
+            e, p4, p5, p2, p3 = bits(mm, 5)
+            v[mm] = (pos(lanes, regs, T, p2 + 2 * p3 + 4 * p4 + 8 * p5), e)
+        m.st(L32, T, v)
     x = [[[None, None] for _ in range(16)] for _ in range(32)]
     for T in range(32):
-        w = [m.ld(L64, T, 16, lb=16 * p3) for p3 in range(2)]
+        w = [m.ld(L256, T, 16, lb=16 * p1) for p1 in range(2)]
         for k in range(16):
-            p01, p2, p3 = k & 3, (k >> 2) & 1, k >> 3
-            x[T][k] = [w[p3][p01 + 8 * p2], w[p3][p01 + 4 + 8 * p2]]
+            p0, p1, p23 = k & 1, (k >> 1) & 1, k >> 2
+            x[T][k] = [w[p1][4 * p23 + 2 * p0], w[p1][4 * p23 + 2 * p0 + 1]]
     final_check(x)
 
 
@@ -179,6 +179,7 @@ def test_n512_one_round_trip():
 # shared-memory exchange of passes 0 and 1 with pass 1 relabelled:
 # (log2N, threads per segment, pass-1 lane bits, pass-1 register bits, address map)
 SHARED = [
+    (10, 64, (6, 7, 8, 0, 1), (2, 3, 4, 5), lambda q: q + 2 * (q >> 6)),
     (11, 128, (8, 0, 1, 2, 7), (3, 4, 5, 6), lambda q: q ^ (((q >> 8) & 1) << 3)),
     (12, 256, (0, 1, 8, 2, 3), (4, 5, 6, 7), lambda q: q + 8 * (q >> 8)),
     (9, 32, (5, 0, 6, 7, 8), (1, 2, 3, 4), lambda q: q + 2 * (q >> 5)),
@@ -206,7 +207,10 @@ def test_relabelled_shared_exchange(log2n, T, lanes, regs, A):
     # the kernels' own address formulas
     for t in range(T):
         for k in range(16):
-            if log2n == 11:
+            if log2n == 10:
+                a0 = t + 66 * k
+                a1 = ((t >> 3) & 3) + 66 * ((t & 7) + 8 * (t >> 5)) + 4 * k
+            elif log2n == 11:
                 a0 = ((t ^ 8) if (k & 2) else t) + 128 * k
                 base = ((t >> 1) & 7) + 128 * ((t >> 4) & 1) + 256 * (t & 1) + 512 * (t >> 5)
                 a1 = base + 8 * ((k & 1) ^ (t & 1)) + 16 * (k >> 1)
@@ -220,9 +224,11 @@ def test_relabelled_shared_exchange(log2n, T, lanes, regs, A):
                                             + 8 * ((t >> 4) & 1)) + 2 * k
             assert a0 == A(pos0(t, k)) and a1 == A(pos1(t, k))
     # the pass-1 twiddle index: position mod the pass's stride, from the relabelled lanes
-    s = {11: 8, 12: 16, 9: 2}[log2n]
+    s = {10: 4, 11: 8, 12: 16, 9: 2}[log2n]
     for t in range(T):
-        if log2n == 11:
+        if log2n == 10:
+            n1 = (t >> 3) & 3
+        elif log2n == 11:
             n1 = (t >> 1) & 7
         elif log2n == 12:
             n1 = (t & 3) + 4 * ((t >> 3) & 1) + 8 * ((t >> 4) & 1)
