@@ -3,7 +3,8 @@
 // A segment of N = 2^LOG2N complex points is transformed by N/16 threads,
 // 16 points each: radix-16 passes (one 16-point DFT per thread, all
 // rotations compile-time constants) followed by one pass of radix 2/4/8/16 at
-// stride 1, exchanging through shared memory between passes.
+// stride 1, exchanging between passes through shared memory or, for the last
+// exchange of kernels with TMEM twiddles (N = 512 .. 4096), through TMEM.
 // * forward passes: decimation in frequency, natural-order input, spectrum
 //   left in mixed-radix digit-reversed order (no reordering step: Sec. 3.3
 //   notes the order is irrelevant to a point-wise product as long as both
@@ -159,17 +160,23 @@ __device__ __forceinline__ void exchange(float2 *x, float2 *buf, int t, const BA
 }
 
 // ---------------------------------------------------------------------------
-// N = 2048 with the TMEM exchange (Geo<11>::TX).  Positions carry 11 bits
-// p0..p10; pass 0 (radix 16 over p7..p10): thread t = p0..p6, register k =
-// p7..p10; pass 1 (radix 16 over p3..p6): register k = p3..p6, thread lanes
-// (bits 0..4) = (p8, p0, p1, p2, p7), warp = p9, p10; pass 2 (radix 8 over
-// p0..p2): thread = p4..p10, register = p0..p3 (the layout of the spectrum).
-// Between passes 1 and 2 only lane and register bits trade places, inside
-// each warp, which the TMEM shapes do without shared memory or a barrier.
+// The TMEM exchange (Geo<>::TX, N = 512 .. 4096, three passes).  Between the
+// last two passes only lane and register bits of a position trade places and
+// the warp bits stay, so that exchange never leaves a warp.  The 16-lane
+// tcgen05 shapes (tmem.cuh) map a thread's registers to other lanes, so a
+// store in one shape and a load in another trade thread bits for column
+// bits: one or two such round trips replace the shared-memory exchange and
+// its barrier.  Pass 1's lanes are relabelled where that makes the trade
+// possible; its shared-memory exchange with pass 0 then uses the per-N
+// layout below (conflict-free for both layouts, 16 distinct 8-byte bank
+// pairs per half warp), and its twiddle index follows the relabelling.
 //
-// Shared-memory exchange of passes 0 and 1: position q at q ^ (p8 << 3)
-// (no padding): conflict-free for both layouts, 16 distinct 8-byte bank
-// pairs per half warp.
+// N = 2048 (Geo<11>::TX): positions carry 11 bits p0..p10; pass 0 (radix 16
+// over p7..p10): thread t = p0..p6, register k = p7..p10; pass 1 (radix 16
+// over p3..p6): register k = p3..p6, thread lanes (bits 0..4) = (p8, p0, p1,
+// p2, p7), warp = p9, p10; pass 2 (radix 8 over p0..p2): thread = p4..p10,
+// register = p0..p3 (the layout of the spectrum).  Shared exchange of passes
+// 0 and 1: position q at q ^ (p8 << 3) (no padding).
 __device__ __forceinline__ int tx11_addr0(int t, int k) { return ((k & 2) ? (t ^ 8) : t) + 128 * k; }
 __device__ __forceinline__ int tx11_addr1(int t, int k) {
     const int base = ((t >> 1) & 7) + 128 * ((t >> 4) & 1) + 256 * (t & 1) + 512 * (t >> 5);

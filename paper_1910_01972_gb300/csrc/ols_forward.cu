@@ -2,8 +2,7 @@
 //
 // Algorithm 2 / Sec. 3.3 of the paper: one kernel; a thread-block owns a
 // segment; the segment's forward FFT is done on chip and its spectrum kept
-// in registers (Sec. 3.3: "stores segment samples, which are now in the
-// frequency domain, into registers"), then for every filter: point-wise
+// on chip (Sec. 3.3 keeps it in registers), then for every filter: point-wise
 // product with the filter's precomputed spectrum, inverse FFT, removal of
 // the M-1 aliased samples, store (Sec. 3.2).
 //
@@ -11,24 +10,24 @@
 // * Each thread holds 16 complex points; a segment of N points uses N/16
 //   threads.  The FFT is a sequence of radix-16 passes (one 16-point DFT per
 //   thread, all rotations compile-time constants) plus one pass of radix
-//   2/4/8/16 at stride 1; passes exchange data through shared memory.
+//   2/4/8/16 at stride 1.
 // * Forward: decimation in frequency, natural-order input, digit-reversed
 //   spectrum.  Inverse: the exact reverse of the passes (decimation in time),
 //   digit-reversed input, natural-order output.  No reordering step (Sec. 3.3
 //   notes the order is irrelevant to the point-wise product).
-// * The spectrum after the last forward pass sits in the registers the first
-//   inverse pass needs, so the per-filter loop starts from registers; the
-//   filter spectra are pre-laid-out so each thread's 16 values arrive in
-//   eight coalesced 16-byte loads.
-// * Shared-memory positions are padded by one slot per 16 (q -> q + q/16):
-//   every pass's accesses are then bank-conflict free for 64-bit loads and
-//   stores, and every address is a per-thread base plus a compile-time
-//   offset.  Two exchange buffers alternate, so one barrier per exchange.
+// * Tensor memory holds, in each thread's own lane, its pass twiddles and the
+//   segment spectrum (read back once per filter), and stages the exchange
+//   between the last two passes (N = 512 .. 4096), which stays inside a warp;
+//   the exchange that crosses warps goes through padded shared memory, one
+//   barrier per exchange (two alternating buffers).
+// * The filter spectra are pre-laid-out so each thread's 16 values arrive in
+//   eight coalesced 16-byte loads; the next filter's spectrum is loaded while
+//   the current one is transformed (except where that spills: see Geo).
 // * Global loads and stores: for each register k, consecutive threads touch
 //   consecutive samples (fully coalesced); the valid-output test is one
 //   unsigned compare per sample.
-// * Persistent grid: resident blocks loop over segments, loading the
-//   twiddle tables into shared memory once.
+// * Persistent grid sized from the SM's registers, shared memory, threads and
+//   TMEM columns: resident blocks loop over segments.
 #include <cuda_runtime.h>
 #include <cstdint>
 
