@@ -69,6 +69,26 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def tc_flops(N, F, nseg):
+    """Tensor-core operations of one split-precision call: every radix-16 pass
+    (log2 N // 4 of them per FFT, one forward per segment and one inverse per
+    segment and filter) is, per row of 16 points (N/16 rows per segment), six
+    MMAs of N = 32, K = 16 (three split products of a 32 x 32 real DFT-16 matrix
+    in two K halves): 6 x 2 x 32 x 16 operations per row."""
+    lg = N.bit_length() - 1
+    return nseg * (lg // 4) * (F + 1) * (N // 16) * 6 * 2 * 32 * 16
+
+
+def tc_peak():
+    """Dense 16-bit tensor peak in TFLOP/s: the measured bf16 burst figure (FP16
+    and BF16 run at the same kind::f16 rate), or the nominal 2250."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured bf16 burst"
+    except Exception:
+        return 2250.0, "nominal"
+
+
 def fp32_flops(N, F, nseg):
     """FP32 operations of one call by the conventional count: 5 N log2 N per
     complex N-point FFT (one forward per segment, one inverse per segment and
@@ -416,6 +436,12 @@ def _tensor_core(res, samples, peak, ns=0):
         tb = 8 * cfg.Ns + 8 * cfg.F * nout
         tcres[name] = {"value": cfg.F * nout / (ms * 1e-3), "unit": UNIT, "ms": ms,
                        "hbm_frac": tb / (ms * 1e-3) / 1e9 / peak, "status": q.status()}
+        if flag:
+            nseg = q.query(cfg.Ns)["nseg"]
+            fl = tc_flops(cfg.N, cfg.F, nseg)
+            tp, tk = tc_peak()
+            tcres[name].update({"tensor_tflops": fl / (ms * 1e-3) / 1e12, "tensor_frac": fl / (ms * 1e-3) / 1e12 / tp,
+                                "tensor_flops_per_launch": fl, "tensor_peak": tp, "tensor_peak_kind": tk})
         torch.cuda.synchronize()
         samples["tc"][name] = y[torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()].cpu().numpy()
         q.close()
