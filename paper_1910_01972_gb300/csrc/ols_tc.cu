@@ -110,7 +110,8 @@ struct Ctx {
     uint32_t phase;        // mbarrier phase expected next
     int ntiles;
     int *status;           // plan status word (error flag)
-    bool failed;
+    bool failed;           // this thread saw a wait expire
+    bool stop;             // some thread of the CTA did (agreed once per filter): leave the loops
 };
 
 // One radix-16 DFT pass on the tensor cores for every thread's 16 values
@@ -163,7 +164,10 @@ __device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
         c.failed = true;
         atomicOr(c.status, 1);
     }
-    c.failed = __syncthreads_or(c.failed) != 0;
+    // no CTA-wide agreement here: every thread goes on along the same path (a
+    // failed thread skips its waits and stores), and the CTA agrees on
+    // stopping once per filter; the barrier before the next MMA issue orders
+    // every thread's read of D before D is overwritten
     c.phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float d[32];
@@ -253,12 +257,13 @@ ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__rest
     c.ntiles = NT;
     c.status = status;
     c.failed = false;
+    c.stop = false;
 
     const int lo = M - 1;
     const float gain = tc::spectrum_gain<LOG2N>();
     int xc = 0;
     const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
-    for (long long blk = blockIdx.x; blk < nblk && !c.failed; blk += gridDim.x) {
+    for (long long blk = blockIdx.x; blk < nblk && !c.stop; blk += gridDim.x) {
         const long long seg = blk * G::SEGS + slot;
         const bool active = seg < nseg;
         const long long start = seg * L;
@@ -277,7 +282,7 @@ ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__rest
         const long long rem = active ? (Nout - start) : 0;
         const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
         const long long obase = start - lo;
-        for (int f = 0; f < F && !c.failed; ++f) {
+        for (int f = 0; f < F && !c.stop; ++f) {
             float2 x[16];
             const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
 #pragma unroll
@@ -295,6 +300,7 @@ ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__rest
                     if ((unsigned)(n - lo) < (unsigned)span) dst[obase + n] = x[k];
                 }
             }
+            c.stop = __syncthreads_or(c.failed) != 0;   // the CTA's agreement, once per filter
         }
     }
     // release TMEM (after a bounded wait for any commit still in flight on failure)
