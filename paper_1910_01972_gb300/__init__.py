@@ -23,26 +23,44 @@ def _stream_ptr(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
-def _require(t: torch.Tensor, name: str, device=None):
+def _check(t: torch.Tensor, name: str, dtype, device):
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch.Tensor" % name)
-    if t.dtype != torch.complex64:
-        raise TypeError("%s must be complex64, got %s" % (name, t.dtype))
-    if not t.is_contiguous():
-        raise ValueError("%s must be contiguous" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, str(dtype).replace("torch.", ""), t.dtype))
     if device is not None and t.device != device:
         raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
 
 
-def _require_real(t: torch.Tensor, name: str, device=None):
-    if not isinstance(t, torch.Tensor):
-        raise TypeError("%s must be a torch.Tensor" % name)
-    if t.dtype != torch.float32:
-        raise TypeError("%s must be float32, got %s" % (name, t.dtype))
+def _lazy(t: torch.Tensor) -> bool:
+    # A conjugate (t.conj()) or negative (e.g. t.conj().imag) view shares its
+    # base's memory and only flags the operation: the bytes at data_ptr() are
+    # not the values the tensor stands for.
+    return t.is_conj() or t.is_neg()
+
+
+def _input(t: torch.Tensor, name: str, device=None, dtype=torch.complex64) -> torch.Tensor:
+    """The tensor whose memory holds the values `t` stands for.  Lazy
+    conjugate / negative views are materialised into a fresh tensor (the
+    kernels read raw memory); any other layout must already be contiguous."""
+    _check(t, name, dtype, device)
+    if _lazy(t):
+        t = t.resolve_conj().resolve_neg()
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
-    if device is not None and t.device != device:
-        raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
+    return t
+
+
+def _output(t: torch.Tensor, name: str, device=None, dtype=torch.complex64) -> torch.Tensor:
+    """A caller-supplied output: written in place, so it must be a plain
+    contiguous tensor (a lazy conjugate or negative view would be read back
+    conjugated or negated)."""
+    _check(t, name, dtype, device)
+    if _lazy(t):
+        raise ValueError("%s must not be a conjugate or negative view (resolve it first)" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
 
 
 def geometry(N: int, M: int, Ns: int):
@@ -97,7 +115,7 @@ class Plan:
 
     def set_filters(self, h: torch.Tensor) -> None:
         """h: [F][M] complex64 on the plan's device."""
-        _require(h, "h", self.device)
+        h = _input(h, "h", self.device)
         if tuple(h.shape) != (self.F, self.M):
             raise ValueError("h must have shape [%d][%d]" % (self.F, self.M))
         check(_native.ols_set_filters(self._h, h.data_ptr(), _stream_ptr(self.device)), "ols_set_filters")
@@ -111,7 +129,7 @@ class Plan:
 
     def convolve(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """Valid-mode convolution: s [Ns] -> y [F][Ns-M+1] (complex64, device)."""
-        _require(s, "s", self.device)
+        s = _input(s, "s", self.device)
         if s.dim() != 1:
             raise ValueError("s must be 1-D")
         Ns = s.shape[0]
@@ -121,27 +139,27 @@ class Plan:
         if out is None:
             out = torch.empty((self.F, Nout), dtype=torch.complex64, device=self.device)
         else:
-            _require(out, "out", self.device)
+            _output(out, "out", self.device)
             if tuple(out.shape) != (self.F, Nout):
                 raise ValueError("out must have shape [F][Ns-M+1]")
         check(_native.ols_convolve(self._h, s.data_ptr(), Ns, out.data_ptr(), _stream_ptr(self.device)),
               "ols_convolve")
         return out
 
-    def _signal(self, s: torch.Tensor) -> int:
-        _require(s, "s", self.device)
+    def _signal(self, s: torch.Tensor):
+        s = _input(s, "s", self.device)
         if s.dim() != 1:
             raise ValueError("s must be 1-D")
         if s.shape[0] < self.M:
             raise ValueError("signal shorter than the filter (Ns < M)")
-        return s.shape[0] - self.M + 1
+        return s, s.shape[0] - self.M + 1
 
     def convolve_power(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """|y|^2 fused into the convolution: s [Ns] -> p [F][Ns-M+1] float32."""
-        Nout = self._signal(s)
+        s, Nout = self._signal(s)
         if out is None:
             out = torch.empty((self.F, Nout), dtype=torch.float32, device=self.device)
-        _require_real(out, "out", self.device)
+        _output(out, "out", self.device, torch.float32)
         if tuple(out.shape) != (self.F, Nout):
             raise ValueError("out must have shape [F][Ns-M+1]")
         check(_native.ols_convolve_power(self._h, s.data_ptr(), s.shape[0], out.data_ptr(),
@@ -153,7 +171,7 @@ class Plan:
         count): records is a device int64 tensor [capacity][2] holding the C
         records (j; f and power packed in the second word, see
         ``decode_candidates``), count a device uint64-as-int64 tensor [1]."""
-        self._signal(s)
+        s, _ = self._signal(s)
         rec = torch.empty((max(int(capacity), 1), 2), dtype=torch.int64, device=self.device)
         cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
         check(_native.ols_convolve_detect(self._h, s.data_ptr(), s.shape[0], float(threshold), rec.data_ptr(),
@@ -164,10 +182,10 @@ class Plan:
     def convolve_derivative(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """Derivative of the convolved output along j (central differences,
         one-sided at the ends): s [Ns] -> d [F][Ns-M+1] complex64."""
-        Nout = self._signal(s)
+        s, Nout = self._signal(s)
         if out is None:
             out = torch.empty((self.F, Nout), dtype=torch.complex64, device=self.device)
-        _require(out, "out", self.device)
+        _output(out, "out", self.device)
         if tuple(out.shape) != (self.F, Nout):
             raise ValueError("out must have shape [F][Ns-M+1]")
         check(_native.ols_convolve_derivative(self._h, s.data_ptr(), s.shape[0], out.data_ptr(),
@@ -176,7 +194,7 @@ class Plan:
 
     def set_filters_real(self, h: torch.Tensor) -> None:
         """Real-to-real plans (flags=OLS_FLAG_R2R): h [F][M] float32 on the plan's device."""
-        _require_real(h, "h", self.device)
+        h = _input(h, "h", self.device, torch.float32)
         if tuple(h.shape) != (self.F, self.M):
             raise ValueError("h must have shape [%d][%d]" % (self.F, self.M))
         check(_native.ols_set_filters_real(self._h, h.data_ptr(), _stream_ptr(self.device)), "ols_set_filters_real")
@@ -184,7 +202,7 @@ class Plan:
 
     def convolve_real(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """Real valid-mode convolution: s [Ns] float32 -> y [F][Ns-M+1] float32 (R2R plans)."""
-        _require_real(s, "s", self.device)
+        s = _input(s, "s", self.device, torch.float32)
         if s.dim() != 1:
             raise ValueError("s must be 1-D")
         Ns = s.shape[0]
@@ -194,7 +212,7 @@ class Plan:
         if out is None:
             out = torch.empty((self.F, Nout), dtype=torch.float32, device=self.device)
         else:
-            _require_real(out, "out", self.device)
+            _output(out, "out", self.device, torch.float32)
             if tuple(out.shape) != (self.F, Nout):
                 raise ValueError("out must have shape [F][Ns-M+1]")
         check(_native.ols_convolve_real(self._h, s.data_ptr(), Ns, out.data_ptr(), _stream_ptr(self.device)),
@@ -205,14 +223,14 @@ class Plan:
         """Host-buffer convolution (pinned CPU tensors give overlapped copies)."""
         if s_host.device.type != "cpu":
             raise ValueError("s_host must be a CPU tensor")
-        _require(s_host, "s_host")
+        s_host = _input(s_host, "s_host")
         Ns = s_host.shape[0]
         if Ns < self.M:
             raise ValueError("signal shorter than the filter (Ns < M)")
         Nout = Ns - self.M + 1
         if out_host is None:
             out_host = torch.empty((self.F, Nout), dtype=torch.complex64, pin_memory=s_host.is_pinned())
-        _require(out_host, "out_host")
+        _output(out_host, "out_host")
         if tuple(out_host.shape) != (self.F, Nout) or out_host.device.type != "cpu":
             raise ValueError("out_host must be a CPU tensor of shape [F][Ns-M+1]")
         check(_native.ols_convolve_host(self._h, s_host.data_ptr(), Ns, out_host.data_ptr(),
@@ -230,9 +248,9 @@ class Plan:
 
         g: [F][Ns-M+1] complex64, the gradient dL/dRe y + i dL/dIm y.
         """
-        _require(g, "g", self.device)
+        g = _input(g, "g", self.device)
         if s is not None:
-            _require(s, "s", self.device)
+            s = _input(s, "s", self.device)
             Ns = s.shape[0]
         if Ns is None:
             raise ValueError("Ns is needed when s is not given")
@@ -320,8 +338,8 @@ class BatchPlan:
 
     def set_filters(self, hs) -> None:
         """hs: list of B device tensors [F[b]][M[b]] complex64."""
+        hs = [_input(h, "h[%d]" % b, self.device) for b, h in enumerate(hs)]
         for b, h in enumerate(hs):
-            _require(h, "h[%d]" % b, self.device)
             if tuple(h.shape) != (self.F[b], self.M[b]):
                 raise ValueError("h[%d] must have shape [%d][%d]" % (b, self.F[b], self.M[b]))
         check(_native.ols_batch_set_filters(self._h, [h.data_ptr() for h in hs], _stream_ptr(self.device)),
@@ -344,14 +362,14 @@ class BatchPlan:
 
     def convolve(self, ss, ys=None):
         """ss: list of B device tensors [Ns[b]]; returns the list of outputs."""
+        ss = [_input(s, "s[%d]" % b, self.device) for b, s in enumerate(ss)]
         for b, s in enumerate(ss):
-            _require(s, "s[%d]" % b, self.device)
             if s.shape != (self.Ns[b],):
                 raise ValueError("s[%d] must have %d samples" % (b, self.Ns[b]))
         if ys is None:
             ys = self.outputs()
         for b, y in enumerate(ys):
-            _require(y, "y[%d]" % b, self.device)
+            _output(y, "y[%d]" % b, self.device)
             if tuple(y.shape) != (self.F[b], self.Nout[b]):
                 raise ValueError("y[%d] has the wrong shape" % b)
         st, yt = self.pointer_table(ss), self.pointer_table(ys)
