@@ -174,6 +174,38 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle legs
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_single_core_rate(s, h, seconds):
+    """Oracle outputs/s on one thread, over a prefix sized to ~seconds."""
+    import oracle
+    n = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        rate, _, desc, _, _ = oracle_rate(s, h, seconds)
+    finally:
+        oracle.set_threads(n)
+    return rate, desc
+
+
 def oracle_rate(s, h, seconds, max_outputs=None):
     """Time the FP64 oracle on a prefix of the workload sized to ~seconds of
     CPU work.  Returns (outputs/s, threads, sample description, prefix Ns, y_ref)."""
@@ -224,7 +256,7 @@ def run_reference(args):
         "config": {"workload": cfg.name, "Ns": cfg.Ns, "F": cfg.F, "M": cfg.M, "N": cfg.N,
                    "note": "FP64 direct convolution (Eq. 1) on host cores; each step is a bounded sample"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": desc + " per step"},
+                         "sample": desc + " per step", "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -723,9 +755,25 @@ def run_ours(args):
             ms_e2e = float(t.item())
         cseg_chunks = plan.last_launch_count()
         h2d = 8 * (cfg.Ns + (cseg_chunks - 1) * (cfg.M - 1))
+        # the host link on this machine, same run: one whole-array copy each way
+        # (pinned), the floor of any pipelined host-buffer convolution
+        link = {}
+        for name, dst, src in (("h2d", s, s_host), ("d2h", y_host, y)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            link[name + "_GBps"] = src.numel() * 8 / (ms * 1e-3) / 1e9
+            link[name + "_ms"] = ms
+        link["floor_ms"] = max(link["h2d_ms"], link["d2h_ms"])
         e2e = {"value": world * outputs / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                "steps": args.e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * cfg.F * Nout,
-               "path": "ols_convolve_host: pinned host buffers, chunked H2D / kernel / D2H on two streams"}
+               "path": "ols_convolve_host: pinned host buffers, chunked H2D / kernel / D2H on two streams",
+               "link": link, "frac_of_link_floor": link["floor_ms"] / ms_e2e}
         del y_host, s_host
     others, samples = (None, None)
     if rank == 0 and world == 1 and not args.no_others and not args.ns:
@@ -750,7 +798,9 @@ def run_ours(args):
         rate, threads, desc, ns, y_ref = oracle_rate(s_np, h_np, args.cpu_seconds)
         got = y[:, : ns - cfg.M + 1].cpu().numpy()
         err = max(float(np.linalg.norm(got[f] - y_ref[f]) / np.linalg.norm(y_ref[f])) for f in range(cfg.F))
+        rate1, desc1 = oracle_single_core_rate(s_np, h_np, min(4.0, args.cpu_seconds / 3))
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+               "cpu_model": cpu_model(), "single_core": {"value": rate1, "unit": UNIT, "sample": desc1},
                "gpu_rel_l2_on_sample": err}
         if samples:
             cpu["other_workloads_rel_l2_on_samples"] = others_errors(samples)

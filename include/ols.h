@@ -33,6 +33,17 @@
  * - Sizes: N (segment / FFT length) is a power of two in [256, 8192]; the
  *   paper's kernels stop at 4096 (Sec. 2), the larger shared memory of the
  *   target allows 8192.  1 <= M <= N, F >= 1, Ns >= M.
+ * - Environment (read when a plan is created, or per call where stated):
+ *   OLS_AUTOTUNE_CACHE (file of measured segment lengths, see ols_autotune);
+ *   OLS_TC_WAIT_LIMIT (polls of each in-loop mbarrier wait of the
+ *   tensor-core forms; default 2^20; a wait that runs out sets the plan's
+ *   status word, see ols_plan_status); OLS_TC_WAIT_NEVER=1 (test switch:
+ *   those waits watch an mbarrier nothing arrives on, so they run out and the
+ *   kernel takes its failure path; its output is then undefined);
+ *   OLS_FAIL_ALLOC=k (host-side fault
+ *   injection: the k-th device allocation of one ols_plan, ols_batch_plan or
+ *   ols_convolve_host call fails and the call returns OLS_ERR_ALLOC, with
+ *   everything it allocated before released; read at each allocation).
  */
 #ifndef OLS_H
 #define OLS_H
@@ -379,13 +390,16 @@ OLS_API int ols_plan_status(ols_plan_t plan, int *status, int reset);
  * as ols_convolve_backward minus the workspace; the scratch is a fixed
  * device array of OLS_NOALLOC_SCRATCH_BYTES inside the library, which every
  * GPU that loads the library holds until the process exits.
- * - Problems whose ols_backward_workspace() exceeds that size are rejected
- *   with OLS_ERR_TOO_LARGE before any work is enqueued.
+ * - The argument checks of ols_convolve_backward run first, in its order;
+ *   then problems whose ols_backward_workspace() exceeds that size are
+ *   rejected with OLS_ERR_TOO_LARGE before any work is enqueued.
  * - The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress, with the plan's device current); make that first
- *   call before any stream capture.  The plan's device must be current
- *   (else OLS_ERR_INVALID).  No cudaMalloc, cudaFree or other allocating
- *   routine is called.
+ *   call before any stream capture.  The address is kept for the life of the
+ *   process: it belongs to the device's primary context, so do not call this
+ *   entry point again after destroying that context (cudaDeviceReset).  The
+ *   plan's device must be current (else OLS_ERR_INVALID).  No cudaMalloc,
+ *   cudaFree or other allocating routine is called.
  * - Every call on a device shares the one array, which keeps the last call's
  *   contents (nothing in it needs to start at zero).  Calls that overlap on
  *   the GPU -- other streams, other threads, other plans -- race on it:

@@ -41,37 +41,6 @@ __device__ __forceinline__ float2 sub_rot(float2 a, float2 b) {
     return INV ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
 }
 
-// Two complex numbers of two different segments in split form:
-// re = (Re a, Re b), im = (Im a, Im b).  Every complex operation on a pair is
-// the same per-lane arithmetic as on one float2, so results are bitwise those
-// of the single-segment code, with one packed instruction per two values.
-struct cpair {
-    float2 re, im;
-};
-__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
-__device__ __forceinline__ cpair cadd(cpair a, cpair b) { return {__fadd2_rn(a.re, b.re), __fadd2_rn(a.im, b.im)}; }
-__device__ __forceinline__ cpair csub(cpair a, cpair b) {
-    return {__fadd2_rn(a.re, neg2(b.re)), __fadd2_rn(a.im, neg2(b.im))};
-}
-template <bool INV>
-__device__ __forceinline__ cpair add_rot(cpair a, cpair b) {
-    return INV ? cpair{__fadd2_rn(a.re, neg2(b.im)), __fadd2_rn(a.im, b.re)}
-               : cpair{__fadd2_rn(a.re, b.im), __fadd2_rn(a.im, neg2(b.re))};
-}
-template <bool INV>
-__device__ __forceinline__ cpair sub_rot(cpair a, cpair b) {
-    return INV ? cpair{__fadd2_rn(a.re, b.im), __fadd2_rn(a.im, neg2(b.re))}
-               : cpair{__fadd2_rn(a.re, neg2(b.im)), __fadd2_rn(a.im, b.re)};
-}
-// a * (wr + i wi) with the factor given as broadcast pairs (wr, wr), (wi, wi)
-__device__ __forceinline__ cpair cmul(cpair a, float2 wr, float2 wi) {
-    return {__ffma2_rn(a.re, wr, neg2(__fmul2_rn(a.im, wi))), __ffma2_rn(a.re, wi, __fmul2_rn(a.im, wr))};
-}
-// a * conj(wr + i wi)
-__device__ __forceinline__ cpair cmulc(cpair a, float2 wr, float2 wi) {
-    return {__ffma2_rn(a.re, wr, __fmul2_rn(a.im, wi)), __ffma2_rn(a.im, wr, neg2(__fmul2_rn(a.re, wi)))};
-}
-
 // a * b
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -89,18 +58,10 @@ template <bool INV>
 __device__ __forceinline__ float2 rot_quarter(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
-template <bool INV>
-__device__ __forceinline__ cpair rot_quarter(cpair a) {
-    return INV ? cpair{neg2(a.im), a.re} : cpair{a.im, neg2(a.re)};
-}
 __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ cpair cneg(cpair a) { return {neg2(a.re), neg2(a.im)}; }
 // a * (wr + i wi) for compile-time constants
 __device__ __forceinline__ float2 cmul_const(float2 a, float wr, float wi) {
     return make_float2(fmaf(a.x, wr, -a.y * wi), fmaf(a.x, wi, a.y * wr));
-}
-__device__ __forceinline__ cpair cmul_const(cpair a, float wr, float wi) {
-    return cmul(a, make_float2(wr, wr), make_float2(wi, wi));
 }
 
 // cos / sin of 2 pi e / 16 for e in [0, 16), as exact-as-float constants.
@@ -212,103 +173,6 @@ __device__ __forceinline__ void dft16(C *x) {
         for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = x[4 * k1 + k2];
 #pragma unroll
     for (int k = 0; k < 16; ++k) x[k] = y[k];
-}
-
-// cos(2 pi e / 64) for e in [0, 64) (exact zeros at e = 16, 48, exact symmetry).
-__device__ __forceinline__ constexpr float c64(int e) {
-    constexpr float t[64] = {
-        1.00000000000000000f, 0.99518472667219693f, 0.98078528040323043f, 0.95694033573220882f,
-        0.92387953251128674f, 0.88192126434835505f, 0.83146961230254524f, 0.77301045336273699f,
-        0.70710678118654757f, 0.63439328416364549f, 0.55557023301960229f, 0.47139673682599781f,
-        0.38268343236508984f, 0.29028467725446233f, 0.19509032201612833f, 0.09801714032956077f,
-        0.0f, -0.09801714032956077f, -0.19509032201612833f, -0.29028467725446233f,
-        -0.38268343236508984f, -0.47139673682599781f, -0.55557023301960229f, -0.63439328416364549f,
-        -0.70710678118654757f, -0.77301045336273699f, -0.83146961230254524f, -0.88192126434835505f,
-        -0.92387953251128674f, -0.95694033573220882f, -0.98078528040323043f, -0.99518472667219693f,
-        -1.00000000000000000f, -0.99518472667219693f, -0.98078528040323043f, -0.95694033573220882f,
-        -0.92387953251128674f, -0.88192126434835505f, -0.83146961230254524f, -0.77301045336273699f,
-        -0.70710678118654757f, -0.63439328416364549f, -0.55557023301960229f, -0.47139673682599781f,
-        -0.38268343236508984f, -0.29028467725446233f, -0.19509032201612833f, -0.09801714032956077f,
-        0.0f, 0.09801714032956077f, 0.19509032201612833f, 0.29028467725446233f,
-        0.38268343236508984f, 0.47139673682599781f, 0.55557023301960229f, 0.63439328416364549f,
-        0.70710678118654757f, 0.77301045336273699f, 0.83146961230254524f, 0.88192126434835505f,
-        0.92387953251128674f, 0.95694033573220882f, 0.98078528040323043f, 0.99518472667219693f};
-    return t[e & 63];
-}
-__device__ __forceinline__ constexpr float s64(int e) { return c64((e + 48) & 63); }  // sin = cos(x - pi/2)
-
-// a * exp(-+ 2 pi i E / 64).
-template <int E, bool INV, class C>
-__device__ __forceinline__ C rot64(C a) {
-    constexpr int e = E & 63;
-    if constexpr ((e & 3) == 0) {
-        return rot16<e / 4, INV>(a);
-    } else {
-        constexpr float wr = c64(e);
-        constexpr float wi = INV ? s64(e) : -s64(e);
-        return cmul_const(a, wr, wi);
-    }
-}
-
-// x[8 K1 + n2] *= W64^(MUL K1 n2) for n2 in [N2, 8): one row of the middle
-// rotation step of an 8-column decomposition.
-template <int MUL, int K1, int N2, bool INV>
-__device__ __forceinline__ void rotate_row(float2 *x) {
-    if constexpr (N2 < 8) {
-        x[8 * K1 + N2] = rot64<MUL * K1 * N2, INV>(x[8 * K1 + N2]);
-        rotate_row<MUL, K1, N2 + 1, INV>(x);
-    }
-}
-// rows K1 in [K1, K1END)
-template <int MUL, int K1, int K1END, bool INV>
-__device__ __forceinline__ void rotate_rows(float2 *x) {
-    if constexpr (K1 < K1END) {
-        rotate_row<MUL, K1, 1, INV>(x);
-        rotate_rows<MUL, K1 + 1, K1END, INV>(x);
-    }
-}
-
-// 32-point DFT in place on x[0..31] (natural order in and out): 32 = 4 x 8.
-// n = 8 n1 + n2, k = k1 + 4 k2:  DFT-4 over n1, rotate by W32^(n2 k1), DFT-8 over n2.
-template <bool INV>
-__device__ __forceinline__ void dft32(float2 *x) {
-#pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2) dft4<INV>(x[n2], x[8 + n2], x[16 + n2], x[24 + n2]);
-    rotate_rows<2, 1, 4, INV>(x);            // W32^(n2 k1) = W64^(2 n2 k1)
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft8<INV>(x + 8 * k1);
-    float2 y[32];
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) y[k1 + 4 * k2] = x[8 * k1 + k2];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) x[k] = y[k];
-}
-
-// 64-point DFT in place on x[0..63] (natural order in and out): 64 = 8 x 8.
-// n = 8 n1 + n2, k = k1 + 8 k2:  DFT-8 over n1, rotate by W64^(n2 k1), DFT-8 over n2.
-template <bool INV>
-__device__ __forceinline__ void dft64(float2 *x) {
-#pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2) {
-        float2 g[8];
-#pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1) g[n1] = x[8 * n1 + n2];
-        dft8<INV>(g);
-#pragma unroll
-        for (int k1 = 0; k1 < 8; ++k1) x[8 * k1 + n2] = g[k1];
-    }
-    rotate_rows<1, 1, 8, INV>(x);            // W64^(n2 k1)
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) dft8<INV>(x + 8 * k1);
-    float2 y[64];
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1)
-#pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) y[k1 + 8 * k2] = x[8 * k1 + k2];
-#pragma unroll
-    for (int k = 0; k < 64; ++k) x[k] = y[k];
 }
 
 // R-point DFT on each of the 16/R consecutive groups of x[0..15].

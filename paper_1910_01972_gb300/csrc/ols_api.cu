@@ -38,21 +38,6 @@ void spectral_order(int log2N, int32_t *nu) {
     }
 }
 
-void spectral_order_w64(int32_t *nu) {
-    for (int q = 0; q < 2048; ++q) nu[q] = (q >> 6) + 32 * (q & 63);
-}
-
-// W_2048^(n' k) for k in [1, 32), n' in [0, 64), index (k-1) 64 + n'.
-static std::vector<float2> w64_twiddles() {
-    std::vector<float2> tw(31 * 64);
-    for (int k = 1; k < 32; ++k)
-        for (int n = 0; n < 64; ++n) {
-            const double a = -2.0 * M_PI * (double)((n * k) % 2048) / 2048.0;
-            tw[(size_t)(k - 1) * 64 + n] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
-    return tw;
-}
-
 static std::vector<float2> forward_twiddles(const PassPlan &pp) {
     // pass p < np-1: entry (k-1) s + n' = W_{16 s}^{n' k}, k in [1, 16), n' in [0, s)
     std::vector<float2> tw((size_t)pp.twn);
@@ -105,6 +90,24 @@ static std::vector<uint16_t> tc_dft16_tables(bool bf16) {
     return out;
 }
 
+static thread_local int t_alloc_depth = 0;
+static thread_local int t_alloc_seq = 0;
+
+AllocScope::AllocScope() {
+    if (t_alloc_depth++ == 0) t_alloc_seq = 0;
+}
+AllocScope::~AllocScope() { --t_alloc_depth; }
+
+cudaError_t dev_alloc_raw(void **p, size_t bytes) {
+    ++t_alloc_seq;
+    const char *v = std::getenv("OLS_FAIL_ALLOC");
+    if (v && std::atoi(v) > 0 && std::atoi(v) == t_alloc_seq) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 static int log2_exact(int64_t N) {
     if (N <= 0 || (N & (N - 1))) return -1;
     int l = 0;
@@ -116,34 +119,8 @@ static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
 static bool aligned4(const void *p) { return ((uintptr_t)p & 3u) == 0; }
 
 // The fused convolution in the plan's arithmetic (FP32 or tensor-core split).
-// The N = 2048 single-warp-per-segment kernel (64 points per thread, one
-// exchange per FFT) is opt-in with OLS_W64_KERNEL=1: on GB300 it measures
-// slower than the 16-points-per-thread kernel (two warps per scheduler cannot
-// hide its latencies).
-static bool use_w64() {
-    const char *v = std::getenv("OLS_W64_KERNEL");
-    return v && v[0] == '1';
-}
-
-// The two-segments-per-thread kernel (N = 2048 or 4096; bitwise the same
-// results) is opt-in with OLS_PAIR_KERNEL=1: it executes 28% fewer
-// instructions, but at 246 registers only 8 warps fit per SM and it measures
-// slower on GB300 than the 16-warp single-segment kernel.
-static bool use_pair() {
-    const char *v = std::getenv("OLS_PAIR_KERNEL");
-    return v && v[0] == '1';
-}
-
 static cudaError_t launch_any(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
                               int64_t Nout, cudaStream_t st, int *launches) {
-    if (p.flags == OLS_FLAG_FP32 && p.tw_pair) {
-        *launches = 1;
-        return pair_launch(p, s, Ns, y, L, nseg, Nout, st);
-    }
-    if (p.flags == OLS_FLAG_FP32 && p.Hk_w64) {
-        *launches = 1;
-        return w64_launch(p, s, Ns, y, L, nseg, Nout, st);
-    }
     if (p.flags == OLS_FLAG_FP32) return launch_forward(p, s, Ns, y, L, nseg, Nout, st, launches);
     *launches = 1;
     return tc_launch(p, s, Ns, y, L, nseg, Nout, st);
@@ -197,11 +174,7 @@ static void free_plan(ols_plan_s *p) {
     if (p->tw64) cudaFree(p->tw64);
     if (p->nu) cudaFree(p->nu);
     if (p->tc_bmat) cudaFree(p->tc_bmat);
-    if (p->Hk_w64) cudaFree(p->Hk_w64);
-    if (p->tw_pair) cudaFree(p->tw_pair);
     if (p->hpack) cudaFree(p->hpack);
-    if (p->tw_w64) cudaFree(p->tw_w64);
-    if (p->nu_w64) cudaFree(p->nu_w64);
     if (p->d_status) cudaFree(p->d_status);
     free_staging(p->stage);
     delete p;
@@ -251,6 +224,7 @@ int ols_spectrum_order(int64_t N, int32_t *nu) {
 }
 
 int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
+    AllocScope scope;
     if (!out) return OLS_ERR_INVALID;
     *out = nullptr;
     if (M < 1 || F < 1) return OLS_ERR_INVALID;
@@ -273,38 +247,28 @@ int ols_plan(ols_plan_t *out, int64_t N, int32_t M, int32_t F, uint32_t flags) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     const bool r2r = flags == OLS_FLAG_R2R;
     const int32_t Fc = r2r ? (F + 1) / 2 : F;       // complex spectra held: paired filters for R2R
-    if (e == cudaSuccess) e = cudaMalloc(&p->Hk, sizeof(float2) * (size_t)Fc * (size_t)N);
-    if (e == cudaSuccess && !r2r) e = cudaMalloc(&p->Htk, sizeof(float2) * (size_t)F * (size_t)N);
-    if (e == cudaSuccess && r2r) e = cudaMalloc(&p->hpack, sizeof(float2) * (size_t)Fc * (size_t)M);
+    if (e == cudaSuccess) e = dev_alloc(&p->Hk, sizeof(float2) * (size_t)Fc * (size_t)N);
+    if (e == cudaSuccess && !r2r) e = dev_alloc(&p->Htk, sizeof(float2) * (size_t)F * (size_t)N);
+    if (e == cudaSuccess && r2r) e = dev_alloc(&p->hpack, sizeof(float2) * (size_t)Fc * (size_t)M);
     if (e == cudaSuccess && r2r) e = r2r_prepare(*p);
-    if (e == cudaSuccess) e = cudaMalloc(&p->tw, sizeof(float2) * (size_t)(p->pp.twn > 0 ? p->pp.twn : 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p->tw64, sizeof(double2) * (size_t)N);
-    if (e == cudaSuccess) e = cudaMalloc(&p->nu, sizeof(int32_t) * (size_t)N);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc(&p->tw, sizeof(float2) * (size_t)(p->pp.twn > 0 ? p->pp.twn : 1));
+    if (e == cudaSuccess) e = dev_alloc(&p->tw64, sizeof(double2) * (size_t)N);
+    if (e == cudaSuccess) e = dev_alloc(&p->nu, sizeof(int32_t) * (size_t)N);
+    if (e == cudaSuccess) e = dev_alloc(&p->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
-    if (e == cudaSuccess && flags == OLS_FLAG_FP32 && (l == 11 || l == 12) && use_pair()) {
-        std::vector<float2> tw = forward_twiddles(p->pp);
-        std::vector<float4> tp(tw.size());
-        for (size_t i = 0; i < tw.size(); ++i) tp[i] = make_float4(tw[i].x, tw[i].x, tw[i].y, tw[i].y);
-        e = cudaMalloc(&p->tw_pair, sizeof(float4) * (tp.empty() ? 1 : tp.size()));
-        if (e == cudaSuccess && !tp.empty())
-            e = cudaMemcpy(p->tw_pair, tp.data(), sizeof(float4) * tp.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = pair_prepare(*p);
+    // In-loop waits of the tensor-core kernel (read at plan creation):
+    // OLS_TC_WAIT_LIMIT (polls) overrides the default limit, and
+    // OLS_TC_WAIT_NEVER=1 points them at an mbarrier nothing arrives on, so a
+    // test can make a wait run out without any fault.
+    p->tc_wait_limit = 1ll << 20;
+    if (const char *wl = std::getenv("OLS_TC_WAIT_LIMIT")) {
+        const long long v = std::atoll(wl);
+        if (v > 0) p->tc_wait_limit = v;
     }
-    if (e == cudaSuccess && flags == OLS_FLAG_FP32 && l == 11 && use_w64()) {
-        std::vector<float2> tw = w64_twiddles();
-        std::vector<int32_t> nu(2048);
-        spectral_order_w64(nu.data());
-        e = cudaMalloc(&p->Hk_w64, sizeof(float2) * (size_t)F * (size_t)N);
-        if (e == cudaSuccess) e = cudaMalloc(&p->tw_w64, sizeof(float2) * tw.size());
-        if (e == cudaSuccess) e = cudaMalloc(&p->nu_w64, sizeof(int32_t) * nu.size());
-        if (e == cudaSuccess) e = cudaMemcpy(p->tw_w64, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(p->nu_w64, nu.data(), sizeof(int32_t) * nu.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = w64_prepare(*p);
-    }
-    if (e == cudaSuccess && flags != OLS_FLAG_FP32) {
+    if (const char *wn = std::getenv("OLS_TC_WAIT_NEVER")) p->tc_wait_never = wn[0] == '1';
+    if (e == cudaSuccess && flags != OLS_FLAG_FP32 && flags != OLS_FLAG_R2R) {
         const std::vector<uint16_t> b = tc_dft16_tables(flags == OLS_FLAG_TC_BF16SPLIT);
-        e = cudaMalloc(&p->tc_bmat, sizeof(uint16_t) * b.size());
+        e = dev_alloc(&p->tc_bmat, sizeof(uint16_t) * b.size());
         if (e == cudaSuccess) e = cudaMemcpy(p->tc_bmat, b.data(), sizeof(uint16_t) * b.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = tc_prepare(*p, flags == OLS_FLAG_TC_BF16SPLIT);
     }
@@ -354,13 +318,10 @@ int ols_set_filters(ols_plan_t plan, const float *h, void *stream) {
     if (!plan || !h || !aligned8(h)) return OLS_ERR_INVALID;
     if (plan->flags == OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
     const float2 *hh = reinterpret_cast<const float2 *>(h);
-    cudaError_t e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0, 0,
+    cudaError_t e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0,
                                    (cudaStream_t)stream);
     if (e == cudaSuccess)
-        e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Htk, 1, 0,
-                           (cudaStream_t)stream);
-    if (e == cudaSuccess && plan->Hk_w64)
-        e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu_w64, plan->tw64, plan->Hk_w64, 0, 1,
+        e = launch_spectra(hh, plan->M, plan->F, plan->log2N, plan->nu, plan->tw64, plan->Htk, 1,
                            (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
     plan->filters_ready = true;
@@ -395,7 +356,7 @@ int ols_set_filters_real(ols_plan_t plan, const float *h, void *stream) {
     const int Fc = (plan->F + 1) / 2;
     cudaError_t e = launch_pack_real_pairs(h, plan->M, plan->F, plan->hpack, (cudaStream_t)stream);
     if (e == cudaSuccess)
-        e = launch_spectra(plan->hpack, plan->M, Fc, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0, 0,
+        e = launch_spectra(plan->hpack, plan->M, Fc, plan->log2N, plan->nu, plan->tw64, plan->Hk, 0,
                            (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
     plan->filters_ready = true;
@@ -478,6 +439,7 @@ int ols_convolve_derivative(ols_plan_t plan, const float *s, int64_t Ns, float *
 }
 
 int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y_host, void *stream) {
+    AllocScope scope;
     if (!plan || !s_host || !y_host || !aligned8(s_host) || !aligned8(y_host)) return OLS_ERR_INVALID;
     if (plan->flags == OLS_FLAG_R2R) return OLS_ERR_UNSUPPORTED;
     if (!plan->filters_ready) return OLS_ERR_NOT_READY;
@@ -510,10 +472,17 @@ int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y
         }
         st.in_cap = st.out_cap = 0;
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-            e = cudaMalloc(&st.in[i], sizeof(float2) * (size_t)cin);
-            if (e == cudaSuccess) e = cudaMalloc(&st.out[i], sizeof(float2) * (size_t)(F * cout));
+            e = dev_alloc(&st.in[i], sizeof(float2) * (size_t)cin);
+            if (e == cudaSuccess) e = dev_alloc(&st.out[i], sizeof(float2) * (size_t)(F * cout));
         }
-        if (e != cudaSuccess) return status_of(e);
+        if (e != cudaSuccess) {
+            for (int i = 0; i < 2; ++i) {
+                if (st.in[i]) cudaFree(st.in[i]);
+                if (st.out[i]) cudaFree(st.out[i]);
+                st.in[i] = st.out[i] = nullptr;
+            }
+            return status_of(e);
+        }
         st.in_cap = cin;
         st.out_cap = F * cout;
     }
@@ -576,8 +545,14 @@ int ols_backward_workspace(ols_plan_t plan, int64_t Ns, int want_ds, int want_dh
     return OLS_OK;
 }
 
-int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const float *g, float *ds, float *dh,
-                          void *workspace, size_t workspace_bytes, void *stream) {
+}  // extern "C"
+
+namespace ols {
+
+// Argument checks of the adjoint, in the order both adjoint entry points
+// report them (pointers, plan state, flags, sizes).
+int backward_validate(ols_plan_t plan, const float *s, int64_t Ns, const float *g, const float *ds,
+                      const float *dh) {
     if (!plan || !g || !aligned8(g) || (!ds && !dh)) return OLS_ERR_INVALID;
     if ((ds && !aligned8(ds)) || (dh && !aligned8(dh))) return OLS_ERR_INVALID;
     if (dh && (!s || !aligned8(s))) return OLS_ERR_INVALID;
@@ -587,6 +562,19 @@ int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const flo
     int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
     if (rc != OLS_OK) return rc;
     if (ds && plan->M - 1 > L) return OLS_ERR_UNSUPPORTED;   // ds overlaps must span two windows at most
+    return OLS_OK;
+}
+
+}  // namespace ols
+
+extern "C" {
+
+int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, const float *g, float *ds, float *dh,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = backward_validate(plan, s, Ns, g, ds, dh);
+    if (rc != OLS_OK) return rc;
+    int64_t L, nseg, Nout;
+    ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
     size_t eb, pb, rb;
     BackwardArgs a{};
     backward_layout(*plan, nseg, ds != nullptr, dh != nullptr, &eb, &pb, &rb, &a.grid);

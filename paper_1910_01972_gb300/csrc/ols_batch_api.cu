@@ -98,9 +98,9 @@ double measure_per_output(int64_t N, int32_t M, int32_t F) {
     const int64_t max_out = (256ll << 20) / (8ll * F);          // <= 256 MB of output
     if (nseg * L > max_out) nseg = std::max<int64_t>(1, max_out / L);
     const int64_t Nout = nseg * L, Ns = Nout + M - 1;
-    cudaError_t e = cudaMalloc(&h, sizeof(float2) * (size_t)F * M);
-    if (e == cudaSuccess) e = cudaMalloc(&s, sizeof(float2) * (size_t)Ns);
-    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(float2) * (size_t)F * Nout);
+    cudaError_t e = dev_alloc(&h, sizeof(float2) * (size_t)F * M);
+    if (e == cudaSuccess) e = dev_alloc(&s, sizeof(float2) * (size_t)Ns);
+    if (e == cudaSuccess) e = dev_alloc(&y, sizeof(float2) * (size_t)F * Nout);
     if (e == cudaSuccess) e = cudaMemset(h, 0, sizeof(float2) * (size_t)F * M);
     if (e == cudaSuccess) e = cudaMemset(s, 0, sizeof(float2) * (size_t)Ns);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -184,6 +184,7 @@ int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N) {
 
 int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t *M, const int32_t *F,
                    const int64_t *N, uint32_t flags) {
+    AllocScope scope;
     if (!out) return OLS_ERR_INVALID;
     *out = nullptr;
     if (B < 1 || !Ns || !M || !F) return OLS_ERR_INVALID;
@@ -269,9 +270,9 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
         g.log2N = 0;
         g.nitems = (long long)items.size();
         g.grid = (int)std::min<long long>(g.nitems, cap);
-        e = cudaMalloc(&bt->d_probs, sizeof(BatchProblemDev) * probs.size());
-        if (e == cudaSuccess) e = cudaMalloc(&bt->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
-        if (e == cudaSuccess) e = cudaMalloc(&bt->d_tickets, sizeof(unsigned long long));
+        e = dev_alloc(&bt->d_probs, sizeof(BatchProblemDev) * probs.size());
+        if (e == cudaSuccess) e = dev_alloc(&bt->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
+        if (e == cudaSuccess) e = dev_alloc(&bt->d_tickets, sizeof(unsigned long long));
         if (e == cudaSuccess)
             e = cudaMemcpy(bt->d_probs, probs.data(), sizeof(BatchProblemDev) * probs.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !items.empty())
@@ -334,9 +335,9 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
         i = j;
     }
     const size_t ng = bt->groups.size();
-    e = cudaMalloc(&bt->d_probs, sizeof(BatchProblemDev) * probs.size());
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_tickets, sizeof(unsigned long long) * ng);
+    e = dev_alloc(&bt->d_probs, sizeof(BatchProblemDev) * probs.size());
+    if (e == cudaSuccess) e = dev_alloc(&bt->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = dev_alloc(&bt->d_tickets, sizeof(unsigned long long) * ng);
     if (e == cudaSuccess)
         e = cudaMemcpy(bt->d_probs, probs.data(), sizeof(BatchProblemDev) * probs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !items.empty())

@@ -34,6 +34,21 @@ void spectral_order(int log2N, int32_t *nu);
 // Model-based segment length (no measurement): minimises (N / L)(log2 N + c).
 int64_t choose_segment_length(int32_t M);
 
+// Every device allocation of the library goes through dev_alloc.  Host-side
+// fault injection for tests: with OLS_FAIL_ALLOC=k (k >= 1) in the
+// environment, the k-th allocation made under one outermost AllocScope (one
+// call of ols_plan, ols_batch_plan or ols_convolve_host) fails as if the
+// device were out of memory; unset or 0, nothing is injected.
+cudaError_t dev_alloc_raw(void **p, size_t bytes);
+template <class T>
+cudaError_t dev_alloc(T **p, size_t bytes) {
+    return dev_alloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+struct AllocScope {      // nests: only the outermost scope restarts the count
+    AllocScope();
+    ~AllocScope();
+};
+
 struct Staging {            // device buffers of ols_convolve_host
     float2 *in[2] = {nullptr, nullptr};
     float2 *out[2] = {nullptr, nullptr};
@@ -96,14 +111,8 @@ struct ols_plan_s {
     int bwd_grid_cap[3] = {0, 0, 0};  // backward kernel: (ds,dh), (ds), (dh)
     int last_launches = 0;
     int tc_grid_cap = 0;         // resident blocks of the tensor-core kernel
-    // N = 2048 single-warp-per-segment kernel (passes 32 x 64)
-    float2 *Hk_w64 = nullptr;    // [F][N] spectra in its register layout
-    float2 *tw_w64 = nullptr;    // W_2048^(n' k), k in [1, 32), n' in [0, 64): index (k-1) 64 + n'
-    int32_t *nu_w64 = nullptr;   // its spectral order
-    int w64_grid_cap = 0;
-    // two-segments-per-thread kernel (N >= 2048)
-    float4 *tw_pair = nullptr;   // twiddle table as broadcast pairs (wr, wr, wi, wi)
-    int pair_grid_cap = 0;
+    long long tc_wait_limit = 0; // polls per in-loop mbarrier wait of the tensor-core kernel
+    bool tc_wait_never = false;  // test switch: in-loop waits watch an mbarrier nothing arrives on
     int post_grid_cap[3] = {0, 0, 0};  // post-processing kernels (power, detect, derivative)
     // real-to-real plans (OLS_FLAG_R2R)
     float2 *hpack = nullptr;     // [ceil(F/2)][M] paired real filters h_{2p} + i h_{2p+1}
@@ -160,18 +169,6 @@ struct BatchGroup {
     const float2 *tw = nullptr;               // twiddles of this N (from one of the problems' plans)
 };
 
-// N = 2048 single-warp-per-segment fused kernel (ols_w64.cu).
-cudaError_t w64_prepare(ols_plan_s &p);
-cudaError_t w64_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
-                       int64_t Nout, cudaStream_t st);
-// Spectral order of the 32 x 64 decomposition: position q = 64 t + j holds t + 32 j.
-void spectral_order_w64(int32_t *nu);
-
-// Two-segments-per-thread fused kernel, split form (ols_pair.cu), N >= 2048.
-cudaError_t pair_prepare(ols_plan_s &p);
-cudaError_t pair_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
-                        int64_t Nout, cudaStream_t st);
-
 // Fused OLS with post-processing of the output (ols_post.cu).
 enum PostMode { POST_POWER = 0, POST_DETECT = 1, POST_DERIV = 2 };
 struct PostArgs {
@@ -207,6 +204,9 @@ cudaError_t launch_forward(const ols_plan_s &p, const float2 *s, int64_t Ns, flo
                            int64_t L, int64_t nseg, int64_t Nout, cudaStream_t st, int *launches);
 // Occupancy / attribute set-up of the forward kernel for p.log2N.
 cudaError_t prepare_forward(ols_plan_s &p);
+// Argument checks shared by ols_convolve_backward and its allocation-free variant.
+int backward_validate(ols_plan_t plan, const float *s, int64_t Ns, const float *g, const float *ds,
+                      const float *dh);
 // Adjoint (ds, dh) of the fused OLS: the window kernel plus the finishing
 // kernel; `launches` receives the number of kernels enqueued.
 cudaError_t prepare_backward(ols_plan_s &p);
@@ -215,9 +215,9 @@ int backward_grid(const ols_plan_s &p, int64_t nseg, bool want_ds, bool want_dh)
 int backward_segs_per_block(int log2N);
 // FP64 precompute kernels.  adjoint != 0 transforms conj(h_f[M-1-k]) instead of h_f[k].
 cudaError_t launch_tw64(double2 *tw64, int N, cudaStream_t st);
-// layout 0: the 16-points-per-thread kernels; layout 1: the N = 2048 64-points-per-thread kernel.
+// Spectra in the 16-points-per-thread register layout of the kernels.
 cudaError_t launch_spectra(const float2 *h, int M, int F, int log2N, const int32_t *nu,
-                           const double2 *tw64, float2 *Hk, int adjoint, int layout, cudaStream_t st);
+                           const double2 *tw64, float2 *Hk, int adjoint, cudaStream_t st);
 cudaError_t launch_spectra_natural(const float2 *Hk, int F, int log2N, const int32_t *nu,
                                    float2 *H, cudaStream_t st);
 

@@ -32,7 +32,10 @@ std::mutex g_scratch_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device (set-up on the
-// first call per device).
+// first call per device).  The address is cached for the life of the
+// process: it belongs to the device's primary context, so a caller that
+// destroys that context (cudaDeviceReset) must not call this entry point
+// again in the same process.
 int scratch_address(int dev, void **out) {
     if (dev < 0 || dev >= kMaxDevices) return OLS_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -49,12 +52,14 @@ int scratch_address(int dev, void **out) {
 
 extern "C" int ols_convolve_backward_noalloc(ols_plan_t plan, const float *s, int64_t Ns, const float *g,
                                              float *ds, float *dh, void *stream) {
-    if (!plan || (!ds && !dh)) return OLS_ERR_INVALID;
+    // the workspace entry point's checks first, so both report the same error
+    int rc = ols::backward_validate(plan, s, Ns, g, ds, dh);
+    if (rc != OLS_OK) return rc;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return OLS_ERR_CUDA;
     if (dev != plan->device) return OLS_ERR_INVALID;      // the plan's device must be current
     size_t need = 0;
-    int rc = ols_backward_workspace(plan, Ns, ds != nullptr, dh != nullptr, &need);
+    rc = ols_backward_workspace(plan, Ns, ds != nullptr, dh != nullptr, &need);
     if (rc != OLS_OK) return rc;
     if (need > (size_t)OLS_NOALLOC_SCRATCH_BYTES) return OLS_ERR_TOO_LARGE;
     void *scratch = nullptr;

@@ -29,7 +29,7 @@ __global__ void tw64_kernel(double2 *tw64, int N) {
 // of the convolution correlates with h).
 __global__ void spectra_kernel(const float2 *__restrict__ h, int M, int F, int log2N,
                                const int32_t *__restrict__ nu_tab, const double2 *__restrict__ tw64,
-                               float2 *__restrict__ Hk, int adjoint, int layout) {
+                               float2 *__restrict__ Hk, int adjoint) {
     const int N = 1 << log2N;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)F * N) return;
@@ -46,14 +46,8 @@ __global__ void spectra_kernel(const float2 *__restrict__ h, int M, int F, int l
         ai = fma((double)hk.x, w.y, fma((double)hk.y, w.x, ai));
     }
     const double inv = 1.0 / (double)N;
-    size_t idx;
-    if (layout == 1) {          // 64 registers per thread: q = 64 t + j, pairs (j, j+1) of 32 threads interleaved
-        const int t = q >> 6, j = q & 63;
-        idx = (size_t)f * N + (size_t)(j >> 1) * 64 + 2 * t + (j & 1);
-    } else {                    // 16 registers per thread: q = 16 t + j
-        const int T = N / 16, t = q >> 4, j = q & 15;
-        idx = (size_t)f * N + (size_t)(j >> 1) * (2 * T) + 2 * t + (j & 1);
-    }
+    const int T = N / 16, t = q >> 4, j = q & 15;
+    const size_t idx = (size_t)f * N + (size_t)(j >> 1) * (2 * T) + 2 * t + (j & 1);
     Hk[idx] = make_float2((float)(ar * inv), (float)(ai * inv));
 }
 
@@ -76,9 +70,9 @@ cudaError_t launch_tw64(double2 *tw64, int N, cudaStream_t st) {
 }
 
 cudaError_t launch_spectra(const float2 *h, int M, int F, int log2N, const int32_t *nu,
-                           const double2 *tw64, float2 *Hk, int adjoint, int layout, cudaStream_t st) {
+                           const double2 *tw64, float2 *Hk, int adjoint, cudaStream_t st) {
     const long long total = (long long)F << log2N;
-    spectra_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(h, M, F, log2N, nu, tw64, Hk, adjoint, layout);
+    spectra_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(h, M, F, log2N, nu, tw64, Hk, adjoint);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,12 @@
 //   by 1/4 (exact), and the filter spectra by 4^(passes-1), which keeps every
 //   16-bit operand below 65504 for inputs with |s| <= 1.42 and unit-L2 filters.
 // Waits on the mbarrier are bounded: on expiry the kernel records an error in
-// the plan's status word, stops, releases its TMEM and returns.
+// the plan's status word, stops, waits (bounded again) for the commit it gave
+// up on, releases its TMEM and returns.  The in-loop limit is a launch
+// argument (the plan's), and so is a test switch that points the in-loop
+// waits at a second mbarrier nothing ever arrives on, so that a test can make
+// a wait run out without any fault; the drain before the TMEM release always
+// watches the real mbarrier with the long limit.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -40,7 +45,7 @@ namespace tc {
 
 constexpr int kCols = 64;            // TMEM columns per 128-row tile: A_hi 16, A_lo 16, D 32
 constexpr int kBytesB = 32 * 32 * 2; // one 32x32 16-bit matrix
-constexpr long long kWaitLimit = 1ll << 20;
+constexpr long long kWaitLimit = 1ll << 20;   // polls; also the drain limit before tcgen05.dealloc
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -105,9 +110,11 @@ struct Ctx {
     uint32_t tmem;         // TMEM base of this CTA
     uint32_t tile_cols;    // column offset of this thread's tile
     uint32_t lane_bits;    // (warp % 4) * 32 << 16
-    uint32_t mbar;         // shared address of the mbarrier
+    uint32_t mbar;         // shared address of the mbarrier the MMAs commit to
+    uint32_t wbar;         // the one in-loop waits watch: mbar, or (test switch) one nothing arrives on
     uint32_t b_smem;       // shared address of the four B matrices (fwd hi, fwd lo, inv hi, inv lo)
-    uint32_t phase;        // mbarrier phase expected next
+    uint32_t phase;        // mbarrier parity expected next; frozen at the pending commit once a wait expired
+    long long wait_limit;  // polls per in-loop wait
     int ntiles;
     int *status;           // plan status word (error flag)
     bool failed;           // this thread saw a wait expire
@@ -154,10 +161,10 @@ __device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
                      : "memory");
     }
     uint32_t done = c.failed ? 1u : 0u;
-    for (long long it = 0; it < kWaitLimit && !done; ++it) {
+    for (long long it = 0; it < c.wait_limit && !done; ++it) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done)
-                     : "r"(c.mbar), "r"(c.phase)
+                     : "r"(c.wbar), "r"(c.phase)
                      : "memory");
     }
     if (!done) {
@@ -167,8 +174,11 @@ __device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
     // no CTA-wide agreement here: every thread goes on along the same path (a
     // failed thread skips its waits and stores), and the CTA agrees on
     // stopping once per filter; the barrier before the next MMA issue orders
-    // every thread's read of D before D is overwritten
-    c.phase ^= 1u;
+    // every thread's read of D before D is overwritten.  A failed thread
+    // keeps c.phase at the parity of the commit it gave up on (the issuing
+    // thread commits nothing after its own failure), which is the one the
+    // drain before the TMEM release must see complete.
+    if (!c.failed) c.phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float d[32];
     tmem_ld32(c.tmem + c.lane_bits + c.tile_cols + 32, d);
@@ -219,13 +229,15 @@ template <int LOG2N, bool BF16>
 __global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, Geo<LOG2N>::MINB)
 ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
               const float2 *__restrict__ twg, const uint16_t *__restrict__ bmat, float2 *__restrict__ y, int M, int F,
-              long long L, long long nseg, long long Nout, int *status) {
+              long long L, long long nseg, long long Nout, int *status, long long wait_limit,
+              int wait_never) {
     using G = Geo<LOG2N>;
     constexpr int NT = G::BLOCK / 128;           // M = 128 tiles per CTA
     constexpr uint32_t NCOLS = NT * tc::kCols;
     static_assert(G::BLOCK % 128 == 0, "the tensor-core form needs 128-thread multiples");
     extern __shared__ float4 smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar_never;   // test switch: no thread or MMA ever arrives here
     __shared__ uint32_t tbase;
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     uint16_t *bsm = reinterpret_cast<uint16_t *>(smem);                     // 4 x 2 KB, 1 KB aligned
@@ -236,7 +248,10 @@ ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__rest
     const float2 *tw = twg;
 
     for (int i = threadIdx.x; i < 4 * tc::kBytesB / 2; i += G::BLOCK) bsm[i] = bmat[i];
-    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar_never)));
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tbase)),
@@ -252,8 +267,10 @@ ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__rest
     c.tile_cols = (uint32_t)(threadIdx.x / 128) * tc::kCols;
     c.lane_bits = (uint32_t)(((threadIdx.x / 32) % 4) * 32) << 16;
     c.mbar = tc::smem_u32(&mbar);
+    c.wbar = wait_never ? tc::smem_u32(&mbar_never) : c.mbar;
     c.b_smem = tc::smem_u32(bsm);
     c.phase = 0;
+    c.wait_limit = wait_limit;
     c.ntiles = NT;
     c.status = status;
     c.failed = false;
@@ -303,13 +320,13 @@ ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__rest
             c.stop = __syncthreads_or(c.failed) != 0;   // the CTA's agreement, once per filter
         }
     }
-    // release TMEM (after a bounded wait for any commit still in flight on failure)
+    // release TMEM (after a bounded wait for the commit a failed thread gave up on)
     if (c.failed) {
         uint32_t done = 0;
         for (long long it = 0; it < tc::kWaitLimit && !done; ++it) {
             asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                          : "=r"(done)
-                         : "r"(c.mbar), "r"(c.phase ^ 1u)
+                         : "r"(c.mbar), "r"(c.phase)
                          : "memory");
         }
     }
@@ -359,7 +376,7 @@ static cudaError_t tc_launch_one(const ols_plan_s &p, const float2 *s, int64_t N
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
     const int grid = (int)(nblk < p.tc_grid_cap ? nblk : p.tc_grid_cap);
     ols_tc_kernel<LOG2N, BF16><<<grid, G::BLOCK, TcGeo<LOG2N>::SMEM, st>>>(
-        s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, p.tc_bmat, y, p.M, p.F, L, nseg, Nout, p.d_status);
+        s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, p.tc_bmat, y, p.M, p.F, L, nseg, Nout, p.d_status, p.tc_wait_limit, p.tc_wait_never ? 1 : 0);
     return cudaGetLastError();
 }
 

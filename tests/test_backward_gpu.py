@@ -180,3 +180,30 @@ def test_backward_errors():
     _, dh2 = big.convolve_backward(s2, g2, False, True)
     assert dh2 is not None
     big.close()
+
+
+def test_workspace_contents_do_not_matter():
+    """Nothing in the caller's workspace needs to start at zero: a NaN-filled
+    workspace gives bit for bit the results of a zero-filled one."""
+    Ns, F, M = 60_000, 8, 129
+    s, h, gy = inputs(9, Ns, F, M)
+    plan = Plan(M, F, 1024)
+    plan.set_filters(dev(h))
+    sd, gd = dev(s), dev(gy)
+    nb = plan.backward_workspace(Ns)
+    st = torch.cuda.current_stream().cuda_stream
+    outs = []
+    for fill in (0.0, float("nan")):
+        ws = torch.full(((nb + 512) // 4,), fill, dtype=torch.float32, device="cuda")
+        wp = (ws.data_ptr() + 255) & ~255
+        ds = torch.empty(Ns, dtype=torch.complex64, device="cuda")
+        dh = torch.empty((F, M), dtype=torch.complex64, device="cuda")
+        rc = _native.ols_convolve_backward(plan.handle, sd.data_ptr(), Ns, gd.data_ptr(), ds.data_ptr(),
+                                           dh.data_ptr(), wp, nb, st)
+        assert rc == _native.OLS_OK
+        torch.cuda.synchronize()
+        outs.append((ds, dh))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    ds_ref, dh_ref = oracle.adjoint(s, h, gy)
+    assert oracle.rel_l2(outs[1][0].cpu().numpy(), ds_ref) <= TOL_DS
+    plan.close()
