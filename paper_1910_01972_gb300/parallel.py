@@ -13,8 +13,12 @@ rows of y and the forward pass needs no communication at all; in the adjoint
 each rank's dh rows are final and the input gradient ds is a sum over ranks
 (one all-reduce of Ns samples).
 
-Collectives use torch.distributed (gloo on CPU tensors, NCCL on CUDA tensors);
-the convolution itself is the caller's (the library's kernels on a GPU).
+``FilterSplit`` is that second split as a product call: each rank plans its
+own block of filters on its own device, runs the library's kernels for it,
+and the rows are gathered (forward) or ds is all-reduced (adjoint).
+
+Collectives use torch.distributed: NCCL on the ranks' CUDA tensors, any other
+backend (gloo) on host copies.
 """
 from __future__ import annotations
 
@@ -88,3 +92,112 @@ def reduce_signal_gradient(ds: torch.Tensor, group=None) -> torch.Tensor:
     out = ds.clone()
     dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
     return out
+
+
+# ------------------------------------------------------------ filter-bank split
+def _device_collectives(group=None) -> bool:
+    import torch.distributed as dist
+    return dist.get_backend(group) == "nccl"
+
+
+def _rows_of(F: int, world: int):
+    return [filter_range(F, world, r) for r in range(world)]
+
+
+def all_gather_rows(local: torch.Tensor, F: int, group=None) -> torch.Tensor:
+    """Every rank's block of rows ([f1-f0][...] as given by filter_range) gathered
+    into the whole [F][...] on every rank, on `local`'s device.  Blocks are
+    padded to the largest block for the collective."""
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    rows = _rows_of(F, world)
+    f0, f1 = rows[rank]
+    if local.shape[0] != f1 - f0:
+        raise ValueError("rank %d holds %d rows, expected %d" % (rank, local.shape[0], f1 - f0))
+    fmax = max(b - a for a, b in rows)
+    comm = local.device if _device_collectives(group) else torch.device("cpu")
+    buf = torch.zeros((fmax,) + tuple(local.shape[1:]), dtype=local.dtype, device=comm)
+    buf[: f1 - f0] = local.to(comm)
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    if buf.is_complex():
+        dist.all_gather([torch.view_as_real(t) for t in parts], torch.view_as_real(buf), group=group)
+    else:
+        dist.all_gather(parts, buf, group=group)
+    whole = torch.cat([parts[r][: b - a] for r, (a, b) in enumerate(rows)], dim=0)
+    return whole.to(local.device)
+
+
+def all_reduce_sum(t: torch.Tensor, group=None) -> torch.Tensor:
+    """Sum of every rank's `t` (all ranks receive it), on t's device."""
+    import torch.distributed as dist
+    comm = t.device if _device_collectives(group) else torch.device("cpu")
+    out = t.to(comm, copy=True)
+    dist.all_reduce(torch.view_as_real(out) if out.is_complex() else out, op=dist.ReduceOp.SUM, group=group)
+    return out.to(t.device)
+
+
+class FilterSplit:
+    """A bank of F filters of M taps split across the ranks of `group`: this
+    rank owns filters [f0, f1) (``filter_range``) and convolves the whole
+    signal with them on the current CUDA device through the library's
+    kernels.  Segments and filters are independent (Sec. 3.2), so the forward
+    pass needs no communication; ``convolve`` gathers the rows so every rank
+    gets y [F][Nout].  In the adjoint each rank's dh rows are final and ds is
+    the sum of every rank's contribution (one all-reduce of Ns samples).
+    A rank without filters (F < world size) contributes zeros."""
+
+    def __init__(self, M: int, F: int, N: int = 0, group=None):
+        import torch.distributed as dist
+        from . import Plan
+        self.group = group
+        self.world, self.rank = dist.get_world_size(group), dist.get_rank(group)
+        self.M, self.F = int(M), int(F)
+        self.f0, self.f1 = filter_range(self.F, self.world, self.rank)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.plan = Plan(self.M, self.f1 - self.f0, N) if self.f1 > self.f0 else None
+        self.N = self.plan.N if self.plan is not None else None
+
+    def close(self):
+        if self.plan is not None:
+            self.plan.close()
+            self.plan = None
+
+    def set_filters(self, h: torch.Tensor) -> None:
+        """h: the whole bank [F][M] complex64 (same on every rank); this rank
+        keeps its own rows."""
+        if tuple(h.shape) != (self.F, self.M):
+            raise ValueError("h must have shape [%d][%d]" % (self.F, self.M))
+        if self.plan is not None:
+            self.plan.set_filters(h[self.f0:self.f1].to(self.device).contiguous())
+
+    def convolve_local(self, s: torch.Tensor) -> torch.Tensor:
+        """This rank's rows of y: [f1-f0][Ns-M+1] (no communication)."""
+        Nout = s.shape[0] - self.M + 1
+        if self.plan is None:
+            return torch.empty((0, Nout), dtype=torch.complex64, device=self.device)
+        return self.plan.convolve(s)
+
+    def convolve(self, s: torch.Tensor) -> torch.Tensor:
+        """y [F][Ns-M+1] on every rank: local rows, then one row gather."""
+        return all_gather_rows(self.convolve_local(s), self.F, self.group)
+
+    def convolve_backward(self, s: torch.Tensor, g: torch.Tensor, want_ds: bool = True, want_dh: bool = True):
+        """g: the whole output gradient [F][Ns-M+1] (same on every rank).
+        Returns (ds [Ns] summed over ranks, dh [F][M] gathered), each None if
+        not wanted."""
+        Ns = s.shape[0]
+        if tuple(g.shape) != (self.F, Ns - self.M + 1):
+            raise ValueError("g must have shape [F][Ns-M+1]")
+        ds_loc = dh_loc = None
+        if self.plan is not None:
+            ds_loc, dh_loc = self.plan.convolve_backward(s, g[self.f0:self.f1].contiguous(), want_ds, want_dh)
+        ds = dh = None
+        if want_ds:
+            if ds_loc is None:
+                ds_loc = torch.zeros(Ns, dtype=torch.complex64, device=self.device)
+            ds = all_reduce_sum(ds_loc, self.group)
+        if want_dh:
+            if dh_loc is None:
+                dh_loc = torch.empty((self.f1 - self.f0, self.M), dtype=torch.complex64, device=self.device)
+            dh = all_gather_rows(dh_loc, self.F, self.group)
+        return ds, dh

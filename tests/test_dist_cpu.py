@@ -1,5 +1,7 @@
 """Multi-rank splitting of one signal (paper_1910_01972_gb300.parallel) on CPU:
-world size 2 over gloo, each rank's shard computed by the FP64 oracle."""
+world size 2 over gloo, each rank's shard computed by the FP64 oracle, the
+shards combined by the module's own collectives (row gather, sum).  The same
+split with the library's kernels on each rank is tests/test_parallel_gpu.py."""
 import os
 import socket
 
@@ -97,21 +99,19 @@ def _filter_worker(rank, world, port, Ns, M, F, q):
         h = (g.normal(size=(F, M)) + 1j * g.normal(size=(F, M))).astype(np.complex64)
         gy = g.normal(size=(F, Ns - M + 1)) + 1j * g.normal(size=(F, Ns - M + 1))
         f0, f1 = parallel.filter_range(F, world, rank)
-        # forward: whole signal, own filters, no communication
+        # forward: whole signal, own filters, no communication; then the
+        # library's row gather (gloo: through host tensors)
         y_loc = oracle.conv(s, h[f0:f1]) if f1 > f0 else np.zeros((0, Ns - M + 1), np.complex128)
-        parts = [None] * world
-        dist.all_gather_object(parts, (f0, y_loc))
+        y = parallel.all_gather_rows(torch.from_numpy(y_loc), F).numpy()
         # adjoint: own dh rows are final, ds is summed over ranks
         if f1 > f0:
             ds_loc, dh_loc = oracle.adjoint(s, h[f0:f1], gy[f0:f1])
         else:
             ds_loc, dh_loc = np.zeros(Ns, np.complex128), np.zeros((0, M), np.complex128)
-        ds_all = parallel.reduce_signal_gradient(torch.from_numpy(ds_loc)).numpy()
-        dh_parts = [None] * world
-        dist.all_gather_object(dh_parts, (f0, dh_loc))
+        ds_all = parallel.all_reduce_sum(torch.from_numpy(ds_loc)).numpy()
+        assert np.array_equal(ds_all, parallel.reduce_signal_gradient(torch.from_numpy(ds_loc)).numpy())
+        dh = parallel.all_gather_rows(torch.from_numpy(dh_loc), F).numpy()
         if rank == 0:
-            y = np.concatenate([p[1] for p in sorted(parts, key=lambda p: p[0])], axis=0)
-            dh = np.concatenate([p[1] for p in sorted(dh_parts, key=lambda p: p[0])], axis=0)
             ds_ref, dh_ref = oracle.adjoint(s, h, gy)
             q.put((bool(np.array_equal(y, oracle.conv(s, h))), bool(np.array_equal(dh, dh_ref)),
                    float(np.max(np.abs(ds_all - ds_ref)) / np.max(np.abs(ds_ref)))))
@@ -119,7 +119,7 @@ def _filter_worker(rank, world, port, Ns, M, F, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("F", [5, 1])
+@pytest.mark.parametrize("F", [5, 1, 2])
 def test_two_rank_filter_split_equals_whole_bank(F):
     """The filter-bank split (no forward communication; ds summed over ranks)
     reproduces the unsplit result; F = 1 leaves one rank without filters."""
