@@ -474,6 +474,15 @@ def _tensor_core(res, samples, peak, ns=0):
             tp, tk = tc_peak()
             tcres[name].update({"tensor_tflops": fl / (ms * 1e-3) / 1e12, "tensor_frac": fl / (ms * 1e-3) / 1e12 / tp,
                                 "tensor_flops_per_launch": fl, "tensor_peak": tp, "tensor_peak_kind": tk})
+            # the workload's stored form: the signal as 16-bit hi / lo planes
+            # (8 bytes per sample, the same bytes as FP32)
+            hi, lo = q.split_signal(s)
+            q.convolve_split(hi, lo, out=y)
+            ms_sp = _time_events(lambda: q.convolve_split(hi, lo, out=y), 5)
+            tcres[name]["split_input"] = {"value": cfg.F * nout / (ms_sp * 1e-3), "unit": UNIT, "ms": ms_sp,
+                                          "hbm_frac": tb / (ms_sp * 1e-3) / 1e9 / peak,
+                                          "note": "ols_convolve_split on planes from ols_split_signal"}
+            del hi, lo
         torch.cuda.synchronize()
         samples["tc"][name] = y[torch.from_numpy(fi).cuda(), torch.from_numpy(ji).cuda()].cpu().numpy()
         q.close()

@@ -174,6 +174,34 @@ OLS_API int ols_get_spectra(ols_plan_t plan, float *H, void *stream);
 OLS_API int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *stream);
 
 /*
+ * Tensor-core plans (OLS_FLAG_TC_FP16SPLIT / _BF16SPLIT) on a signal STORED
+ * split: every sample x = (x_hi + x_lo), each part a pair of 16-bit numbers
+ * (Re, Im) in the plan's 16-bit type (FP16 or BF16).  The paper has no
+ * split storage; it is the input form of the split-precision convolution
+ * (the tensor-core MMAs take 16-bit operands, Sec. 3.3's FFT stages as
+ * matrix products), 8 bytes per sample like FP32.
+ * s_hi, s_lo: device [Ns] planes of 32-bit words, each word one sample's
+ * (Re, Im) pair, Re in the low half (4-byte aligned).  y: device
+ * [F][Ns-M+1] complex FP32.  The first forward FFT stage takes the planes
+ * as its tensor-core operands directly; the result equals ols_convolve on
+ * the FP32 signal x_hi + x_lo when the planes come from ols_split_signal
+ * (bit for bit).  Errors: INVALID (NULL / misaligned pointer, Ns < M),
+ * UNSUPPORTED (not a tensor-core plan), NOT_READY, CUDA.
+ */
+OLS_API int ols_convolve_split(ols_plan_t plan, const void *s_hi, const void *s_lo, int64_t Ns, float *y,
+                               void *stream);
+
+/*
+ * The split storage of an FP32 signal for ols_convolve_split: for the real
+ * and imaginary part x of every sample, x_hi = round16(x), x_lo =
+ * round16(x - x_hi) (round to nearest even; the 16-bit type of the plan).
+ * s: device [Ns] complex FP32 (8-byte aligned); s_hi, s_lo: device [Ns]
+ * planes as above.  Errors: INVALID, UNSUPPORTED (not a tensor-core plan),
+ * CUDA.
+ */
+OLS_API int ols_split_signal(ols_plan_t plan, const float *s, int64_t Ns, void *s_hi, void *s_lo, void *stream);
+
+/*
  * Filter spectra of a real-to-real plan (flags OLS_FLAG_R2R).  h: device
  * [F][M] real FP32 (4-byte aligned).  The filters are taken in pairs as the
  * complex sequences g_p = h_{2p} + i h_{2p+1}, p < ceil(F/2) (the partner of

@@ -146,6 +146,38 @@ class Plan:
               "ols_convolve")
         return out
 
+    def split_signal(self, s: torch.Tensor):
+        """Tensor-core plans: the stored split form (hi, lo) of s [Ns]
+        complex64, two int32 tensors [Ns] each holding one sample's 16-bit
+        (Re, Im) pair (see ols_split_signal)."""
+        s = _input(s, "s", self.device)
+        hi = torch.empty(s.shape[0], dtype=torch.int32, device=self.device)
+        lo = torch.empty_like(hi)
+        check(_native.ols_split_signal(self._h, s.data_ptr(), s.shape[0], hi.data_ptr(), lo.data_ptr(),
+                                       _stream_ptr(self.device)), "ols_split_signal")
+        return hi, lo
+
+    def convolve_split(self, s_hi: torch.Tensor, s_lo: torch.Tensor, out: torch.Tensor | None = None):
+        """Tensor-core plans: convolution of a signal stored split (planes as
+        returned by split_signal): -> y [F][Ns-M+1] complex64."""
+        s_hi = _input(s_hi, "s_hi", self.device, torch.int32)
+        s_lo = _input(s_lo, "s_lo", self.device, torch.int32)
+        if s_hi.dim() != 1 or s_hi.shape != s_lo.shape:
+            raise ValueError("s_hi and s_lo must be 1-D and of one length")
+        Ns = s_hi.shape[0]
+        if Ns < self.M:
+            raise ValueError("signal shorter than the filter (Ns < M)")
+        Nout = Ns - self.M + 1
+        if out is None:
+            out = torch.empty((self.F, Nout), dtype=torch.complex64, device=self.device)
+        else:
+            _output(out, "out", self.device)
+            if tuple(out.shape) != (self.F, Nout):
+                raise ValueError("out must have shape [F][Ns-M+1]")
+        check(_native.ols_convolve_split(self._h, s_hi.data_ptr(), s_lo.data_ptr(), Ns, out.data_ptr(),
+                                         _stream_ptr(self.device)), "ols_convolve_split")
+        return out
+
     def _signal(self, s: torch.Tensor):
         s = _input(s, "s", self.device)
         if s.dim() != 1:

@@ -48,6 +48,8 @@ SIGNATURES = [
     ("ols_get_spectra", cint, [vp, vp, vp]),
     ("ols_convolve", cint, [vp, vp, i64, vp, vp]),
     ("ols_convolve_host", cint, [vp, vp, i64, vp, vp]),
+    ("ols_convolve_split", cint, [vp, vp, vp, i64, vp, vp]),
+    ("ols_split_signal", cint, [vp, vp, i64, vp, vp, vp]),
     ("ols_convolve_power", cint, [vp, vp, i64, vp, vp]),
     ("ols_convolve_detect", cint, [vp, vp, i64, ctypes.c_float, vp, i64, vp, vp]),
     ("ols_convolve_derivative", cint, [vp, vp, i64, vp, vp]),
@@ -184,6 +186,14 @@ def ols_backward_workspace(plan, Ns: int, want_ds: bool, want_dh: bool):
 def ols_convolve_backward(plan, s_ptr, Ns: int, g_ptr: int, ds_ptr, dh_ptr, ws_ptr, ws_bytes: int,
                           stream: int) -> int:
     return lib().ols_convolve_backward(plan, s_ptr, Ns, g_ptr, ds_ptr, dh_ptr, ws_ptr, ws_bytes, stream)
+
+
+def ols_convolve_split(plan, hi_ptr: int, lo_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
+    return lib().ols_convolve_split(plan, hi_ptr, lo_ptr, Ns, y_ptr, stream)
+
+
+def ols_split_signal(plan, s_ptr: int, Ns: int, hi_ptr: int, lo_ptr: int, stream: int) -> int:
+    return lib().ols_split_signal(plan, s_ptr, Ns, hi_ptr, lo_ptr, stream)
 
 
 def ols_convolve_backward_noalloc(plan, s_ptr, Ns: int, g_ptr: int, ds_ptr, dh_ptr, stream: int) -> int:

@@ -123,7 +123,9 @@ static cudaError_t launch_any(const ols_plan_s &p, const float2 *s, int64_t Ns, 
                               int64_t Nout, cudaStream_t st, int *launches) {
     if (p.flags == OLS_FLAG_FP32) return launch_forward(p, s, Ns, y, L, nseg, Nout, st, launches);
     *launches = 1;
-    return tc_launch(p, s, Ns, y, L, nseg, Nout, st);
+    TcSignal sg;
+    sg.s = s;
+    return tc_launch(p, sg, Ns, y, L, nseg, Nout, st);
 }
 
 static int status_of(cudaError_t e) {
@@ -347,6 +349,32 @@ int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, void *st
     cudaError_t e = launch_any(*plan, reinterpret_cast<const float2 *>(s), Ns, reinterpret_cast<float2 *>(y), L,
                                nseg, Nout, (cudaStream_t)stream, &launches);
     plan->last_launches = launches;
+    return status_of(e);
+}
+
+int ols_split_signal(ols_plan_t plan, const float *s, int64_t Ns, void *s_hi, void *s_lo, void *stream) {
+    if (!plan || !s || !s_hi || !s_lo || !aligned8(s) || !aligned4(s_hi) || !aligned4(s_lo) || Ns < 0)
+        return OLS_ERR_INVALID;
+    if (plan->flags != OLS_FLAG_TC_FP16SPLIT && plan->flags != OLS_FLAG_TC_BF16SPLIT) return OLS_ERR_UNSUPPORTED;
+    if (Ns == 0) return OLS_OK;
+    cudaError_t e = launch_split_signal(reinterpret_cast<const float2 *>(s), Ns,
+                                        plan->flags == OLS_FLAG_TC_BF16SPLIT, static_cast<uint32_t *>(s_hi),
+                                        static_cast<uint32_t *>(s_lo), plan->sm_count, (cudaStream_t)stream);
+    return status_of(e);
+}
+
+int ols_convolve_split(ols_plan_t plan, const void *s_hi, const void *s_lo, int64_t Ns, float *y, void *stream) {
+    if (!plan || !s_hi || !s_lo || !y || !aligned4(s_hi) || !aligned4(s_lo) || !aligned8(y)) return OLS_ERR_INVALID;
+    if (plan->flags != OLS_FLAG_TC_FP16SPLIT && plan->flags != OLS_FLAG_TC_BF16SPLIT) return OLS_ERR_UNSUPPORTED;
+    if (!plan->filters_ready) return OLS_ERR_NOT_READY;
+    int64_t L, nseg, Nout;
+    int rc = ols_geometry(plan->N, plan->M, Ns, &L, &nseg, &Nout);
+    if (rc != OLS_OK) return rc;
+    TcSignal sg;
+    sg.hi = static_cast<const uint32_t *>(s_hi);
+    sg.lo = static_cast<const uint32_t *>(s_lo);
+    cudaError_t e = tc_launch(*plan, sg, Ns, reinterpret_cast<float2 *>(y), L, nseg, Nout, (cudaStream_t)stream);
+    plan->last_launches = 1;
     return status_of(e);
 }
 

@@ -111,6 +111,7 @@ struct ols_plan_s {
     int bwd_grid_cap[3] = {0, 0, 0};  // backward kernel: (ds,dh), (ds), (dh)
     int last_launches = 0;
     int tc_grid_cap = 0;         // resident blocks of the tensor-core kernel
+    int tc_split_grid_cap = 0;   // the same for its pre-split-input form
     long long tc_wait_limit = 0; // polls per in-loop mbarrier wait of the tensor-core kernel
     bool tc_wait_never = false;  // test switch: in-loop waits watch an mbarrier nothing arrives on
     int post_grid_cap[3] = {0, 0, 0};  // post-processing kernels (power, detect, derivative)
@@ -190,10 +191,17 @@ cudaError_t r2r_prepare(ols_plan_s &p);
 cudaError_t r2r_launch(const ols_plan_s &p, const float *s, int64_t Ns, float *y, int64_t L, int64_t nseg,
                        int64_t Nout, cudaStream_t st);
 
-// Tensor-core split-precision form (ols_tc.cu).
+// Tensor-core split-precision form (ols_tc.cu).  The signal is either FP32
+// (s) or already split into 16-bit hi / lo planes of (Re, Im) pairs.
+struct TcSignal {
+    const float2 *s = nullptr;
+    const uint32_t *hi = nullptr, *lo = nullptr;
+};
 cudaError_t tc_prepare(ols_plan_s &p, bool bf16);
-cudaError_t tc_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
+cudaError_t tc_launch(const ols_plan_s &p, const TcSignal &sg, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
                       int64_t Nout, cudaStream_t st);
+cudaError_t launch_split_signal(const float2 *s, int64_t Ns, bool bf16, uint32_t *hi, uint32_t *lo, int sm_count,
+                                cudaStream_t st);
 
 cudaError_t batched_prepare(int log2N, int sm_count, int *grid_cap, int *segs);
 cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, float2 *const *y_ptrs,

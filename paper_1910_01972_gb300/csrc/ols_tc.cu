@@ -121,16 +121,11 @@ struct Ctx {
     bool stop;             // some thread of the CTA did (agreed once per filter): leave the loops
 };
 
-// One radix-16 DFT pass on the tensor cores for every thread's 16 values
-// (x scaled by `scale` first).  Collective over the CTA.
+// One radix-16 DFT pass on the tensor cores for every thread's 16 values,
+// given as the split rows of A: hi[w] / lo[w] pack (Re x_2w, Re x_2w+1) for
+// w < 8 and (Im x_2(w-8), Im x_2(w-8)+1) for w >= 8.  Collective over the CTA.
 template <bool INV, bool BF16>
-__device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
-    uint32_t hi[16], lo[16];
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        split2<BF16>(x[2 * w].x * scale, x[2 * w + 1].x * scale, hi[w], lo[w]);
-        split2<BF16>(x[2 * w].y * scale, x[2 * w + 1].y * scale, hi[8 + w], lo[8 + w]);
-    }
+__device__ __forceinline__ void dft16_rows(const uint32_t *hi, const uint32_t *lo, float2 *x, Ctx &c) {
     const uint32_t a_hi = c.tmem + c.lane_bits + c.tile_cols;
     tmem_st16(a_hi, hi);
     tmem_st16(a_hi + 16, lo);
@@ -186,11 +181,44 @@ __device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
     for (int j = 0; j < 16; ++j) x[j] = make_float2(d[j], d[16 + j]);
 }
 
-template <int LOG2N, int P, bool BF16>
-__device__ __forceinline__ void tc_forward_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc, Ctx &c) {
+// The same pass on FP32 values (x scaled by `scale` first), split here.
+template <bool INV, bool BF16>
+__device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        split2<BF16>(x[2 * w].x * scale, x[2 * w + 1].x * scale, hi[w], lo[w]);
+        split2<BF16>(x[2 * w].y * scale, x[2 * w + 1].y * scale, hi[8 + w], lo[8 + w]);
+    }
+    dft16_rows<INV, BF16>(hi, lo, x, c);
+}
+
+// Rows of A from samples already stored split: hs[k] / ls[k] hold
+// (Re, Im) of point k as two 16-bit numbers; A wants (Re x_2w, Re x_2w+1).
+__device__ __forceinline__ void rows_from_planes(const uint32_t *hs, const uint32_t *ls, uint32_t *hi, uint32_t *lo) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        hi[w] = __byte_perm(hs[2 * w], hs[2 * w + 1], 0x5410);       // low halves: Re
+        hi[8 + w] = __byte_perm(hs[2 * w], hs[2 * w + 1], 0x7632);   // high halves: Im
+        lo[w] = __byte_perm(ls[2 * w], ls[2 * w + 1], 0x5410);
+        lo[8 + w] = __byte_perm(ls[2 * w], ls[2 * w + 1], 0x7632);
+    }
+}
+
+// Forward passes P.. on x.  With PRE (pre-split input) the first pass takes
+// its A rows as given (rows_hi / rows_lo) instead of splitting x.
+template <int LOG2N, int P, bool BF16, bool PRE = false>
+__device__ __forceinline__ void tc_forward_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc, Ctx &c,
+                                                  const uint32_t *rows_hi = nullptr, const uint32_t *rows_lo = nullptr) {
     using G = Geo<LOG2N>;
-    if constexpr (G::radix(P) == 16) dft16<false, BF16>(x, 1.0f, c);
-    else dft_groups<G::radix(P), false>(x);
+    static_assert(G::radix(0) == 16, "the first forward pass is radix 16 for every supported N");
+    if constexpr (P == 0 && PRE) {
+        dft16_rows<false, BF16>(rows_hi, rows_lo, x, c);
+    } else if constexpr (G::radix(P) == 16) {
+        dft16<false, BF16>(x, 1.0f, c);
+    } else {
+        dft_groups<G::radix(P), false>(x);
+    }
     if constexpr (P < G::NP - 1) {
         twiddle<LOG2N, P, false>(x, tw, t);
         exchange<LOG2N, P, P + 1>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
@@ -225,9 +253,12 @@ __host__ __device__ constexpr float spectrum_gain() {
 
 }  // namespace tc
 
-template <int LOG2N, bool BF16>
+// PRE: the signal comes as two planes of 16-bit (Re, Im) pairs, hi and lo
+// (sig_hi / sig_lo, one 32-bit word per sample), instead of FP32 (sig).
+template <int LOG2N, bool BF16, bool PRE>
 __global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, Geo<LOG2N>::MINB)
-ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
+ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_hi, const uint32_t *__restrict__ sig_lo,
+              long long Ns, const float4 *__restrict__ Hk,
               const float2 *__restrict__ twg, const uint16_t *__restrict__ bmat, float2 *__restrict__ y, int M, int F,
               long long L, long long nseg, long long Nout, int *status, long long wait_limit,
               int wait_never) {
@@ -285,15 +316,26 @@ ols_tc_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__rest
         const bool active = seg < nseg;
         const long long start = seg * L;
         float2 X[16];
-        {
-            const long long avail = active ? (Ns - start) : 0;
-            const int lim = (int)(avail < G::N ? avail : G::N);
+        const long long avail = active ? (Ns - start) : 0;
+        const int lim = (int)(avail < G::N ? avail : G::N);
+        if constexpr (PRE) {
+            uint32_t hs[16], ls[16], rh[16], rl[16];
+            const uint32_t *sh = sig_hi + (active ? start : 0) + t, *sl = sig_lo + (active ? start : 0) + t;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const bool in = k * G::T + t < lim;
+                hs[k] = in ? __ldg(sh + k * G::T) : 0u;
+                ls[k] = in ? __ldg(sl + k * G::T) : 0u;
+            }
+            tc::rows_from_planes(hs, ls, rh, rl);
+            tc::tc_forward_passes<LOG2N, 0, BF16, true>(X, bufs, tw, t, xc, c, rh, rl);
+        } else {
             const float2 *src = sig + (active ? start : 0) + t;
 #pragma unroll
             for (int k = 0; k < 16; ++k)
                 X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+            tc::tc_forward_passes<LOG2N, 0, BF16>(X, bufs, tw, t, xc, c);
         }
-        tc::tc_forward_passes<LOG2N, 0, BF16>(X, bufs, tw, t, xc, c);
 #pragma unroll
         for (int k = 0; k < 16; ++k) X[k] = make_float2(X[k].x * gain, X[k].y * gain);
         const long long rem = active ? (Nout - start) : 0;
@@ -343,18 +385,25 @@ struct TcGeo {
                                                                                Geo<LOG2N>::PADN);
 };
 
-template <int LOG2N, bool BF16>
-static cudaError_t tc_prepare_one(ols_plan_s &p) {
-    cudaError_t e = cudaFuncSetAttribute(ols_tc_kernel<LOG2N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int LOG2N, bool BF16, bool PRE>
+static cudaError_t tc_prepare_kernel(int sm_count, int *grid_cap) {
+    cudaError_t e = cudaFuncSetAttribute(ols_tc_kernel<LOG2N, BF16, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)TcGeo<LOG2N>::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     const int cols = (Geo<LOG2N>::BLOCK / 128) * tc::kCols;   // TMEM holds every resident CTA's columns
-    e = resident_blocks_tmem(ols_tc_kernel<LOG2N, BF16>, Geo<LOG2N>::BLOCK, TcGeo<LOG2N>::SMEM, cols, &per_sm);
+    e = resident_blocks_tmem(ols_tc_kernel<LOG2N, BF16, PRE>, Geo<LOG2N>::BLOCK, TcGeo<LOG2N>::SMEM, cols, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    p.tc_grid_cap = per_sm * p.sm_count;
+    *grid_cap = per_sm * sm_count;
     return cudaSuccess;
+}
+
+template <int LOG2N, bool BF16>
+static cudaError_t tc_prepare_one(ols_plan_s &p) {
+    cudaError_t e = tc_prepare_kernel<LOG2N, BF16, false>(p.sm_count, &p.tc_grid_cap);
+    if (e == cudaSuccess) e = tc_prepare_kernel<LOG2N, BF16, true>(p.sm_count, &p.tc_split_grid_cap);
+    return e;
 }
 
 cudaError_t tc_prepare(ols_plan_s &p, bool bf16) {
@@ -369,35 +418,66 @@ cudaError_t tc_prepare(ols_plan_s &p, bool bf16) {
     }
 }
 
-template <int LOG2N, bool BF16>
-static cudaError_t tc_launch_one(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L,
+template <int LOG2N, bool BF16, bool PRE>
+static cudaError_t tc_launch_one(const ols_plan_s &p, const TcSignal &sg, int64_t Ns, float2 *y, int64_t L,
                                  int64_t nseg, int64_t Nout, cudaStream_t st) {
     using G = Geo<LOG2N>;
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
-    const int grid = (int)(nblk < p.tc_grid_cap ? nblk : p.tc_grid_cap);
-    ols_tc_kernel<LOG2N, BF16><<<grid, G::BLOCK, TcGeo<LOG2N>::SMEM, st>>>(
-        s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, p.tc_bmat, y, p.M, p.F, L, nseg, Nout, p.d_status, p.tc_wait_limit, p.tc_wait_never ? 1 : 0);
+    const int cap = PRE ? p.tc_split_grid_cap : p.tc_grid_cap;
+    const int grid = (int)(nblk < cap ? nblk : cap);
+    ols_tc_kernel<LOG2N, BF16, PRE><<<grid, G::BLOCK, TcGeo<LOG2N>::SMEM, st>>>(
+        sg.s, sg.hi, sg.lo, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, p.tc_bmat, y, p.M, p.F, L, nseg, Nout,
+        p.d_status, p.tc_wait_limit, p.tc_wait_never ? 1 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t tc_launch(const ols_plan_s &p, const float2 *s, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
-                      int64_t Nout, cudaStream_t st) {
+template <int LOG2N>
+static cudaError_t tc_launch_n(const ols_plan_s &p, const TcSignal &sg, int64_t Ns, float2 *y, int64_t L,
+                               int64_t nseg, int64_t Nout, cudaStream_t st) {
     const bool bf16 = (p.flags & OLS_FLAG_TC_BF16SPLIT) != 0;
+    const bool pre = sg.hi != nullptr;
+    if (bf16) return pre ? tc_launch_one<LOG2N, true, true>(p, sg, Ns, y, L, nseg, Nout, st)
+                         : tc_launch_one<LOG2N, true, false>(p, sg, Ns, y, L, nseg, Nout, st);
+    return pre ? tc_launch_one<LOG2N, false, true>(p, sg, Ns, y, L, nseg, Nout, st)
+               : tc_launch_one<LOG2N, false, false>(p, sg, Ns, y, L, nseg, Nout, st);
+}
+
+cudaError_t tc_launch(const ols_plan_s &p, const TcSignal &sg, int64_t Ns, float2 *y, int64_t L, int64_t nseg,
+                      int64_t Nout, cudaStream_t st) {
     switch (p.log2N) {
-        case 8: return bf16 ? tc_launch_one<8, true>(p, s, Ns, y, L, nseg, Nout, st)
-                            : tc_launch_one<8, false>(p, s, Ns, y, L, nseg, Nout, st);
-        case 9: return bf16 ? tc_launch_one<9, true>(p, s, Ns, y, L, nseg, Nout, st)
-                            : tc_launch_one<9, false>(p, s, Ns, y, L, nseg, Nout, st);
-        case 10: return bf16 ? tc_launch_one<10, true>(p, s, Ns, y, L, nseg, Nout, st)
-                             : tc_launch_one<10, false>(p, s, Ns, y, L, nseg, Nout, st);
-        case 11: return bf16 ? tc_launch_one<11, true>(p, s, Ns, y, L, nseg, Nout, st)
-                             : tc_launch_one<11, false>(p, s, Ns, y, L, nseg, Nout, st);
-        case 12: return bf16 ? tc_launch_one<12, true>(p, s, Ns, y, L, nseg, Nout, st)
-                             : tc_launch_one<12, false>(p, s, Ns, y, L, nseg, Nout, st);
-        case 13: return bf16 ? tc_launch_one<13, true>(p, s, Ns, y, L, nseg, Nout, st)
-                             : tc_launch_one<13, false>(p, s, Ns, y, L, nseg, Nout, st);
+        case 8: return tc_launch_n<8>(p, sg, Ns, y, L, nseg, Nout, st);
+        case 9: return tc_launch_n<9>(p, sg, Ns, y, L, nseg, Nout, st);
+        case 10: return tc_launch_n<10>(p, sg, Ns, y, L, nseg, Nout, st);
+        case 11: return tc_launch_n<11>(p, sg, Ns, y, L, nseg, Nout, st);
+        case 12: return tc_launch_n<12>(p, sg, Ns, y, L, nseg, Nout, st);
+        case 13: return tc_launch_n<13>(p, sg, Ns, y, L, nseg, Nout, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// The stored split form of a signal: hi = rn16(x), lo = rn16(x - hi) for the
+// real and the imaginary part of every sample, written as 16-bit (Re, Im)
+// pairs, one plane each -- the same rounding the kernel applies when it
+// splits FP32 values itself.
+template <bool BF16>
+__global__ void split_signal_kernel(const float2 *__restrict__ s, long long Ns, uint32_t *__restrict__ hi,
+                                    uint32_t *__restrict__ lo) {
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < Ns; n += (long long)gridDim.x * blockDim.x) {
+        const float2 v = s[n];
+        uint32_t h, l;
+        tc::split2<BF16>(v.x, v.y, h, l);
+        hi[n] = h;
+        lo[n] = l;
+    }
+}
+
+cudaError_t launch_split_signal(const float2 *s, int64_t Ns, bool bf16, uint32_t *hi, uint32_t *lo, int sm_count,
+                                cudaStream_t st) {
+    const long long want = (Ns + 255) / 256;
+    const int grid = (int)(want < 8ll * sm_count ? (want > 0 ? want : 1) : 8ll * sm_count);
+    if (bf16) split_signal_kernel<true><<<grid, 256, 0, st>>>(s, Ns, hi, lo);
+    else split_signal_kernel<false><<<grid, 256, 0, st>>>(s, Ns, hi, lo);
+    return cudaGetLastError();
 }
 
 }  // namespace ols
