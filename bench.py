@@ -395,6 +395,20 @@ def _batched(res, samples, peak):
     torch.cuda.synchronize()
     outs = sum(f * n for f, n in zip(spec.F, bp.Nout))
     ms_g = _time_events(graph.replay, 5)
+    # the tile schedule: tuned runs of tiles per item against one tile per item
+    ms_tuned = _time_events(lambda: bp.launch(st_t, yt_t), 5)
+    b1 = BatchPlan(spec.Ns, spec.M, spec.F, N=bp.N, tiles=[1] * bp.B)
+    b1.set_filters([torch.from_numpy(h).cuda() for h in hs])
+    b1.launch(st_t, yt_t)
+    ms_one = _time_events(lambda: b1.launch(st_t, yt_t), 5)
+    items_one = sum(b1.items)
+    b1.close()
+    hist = {}
+    for r in bp.tiles:
+        hist[str(r)] = hist.get(str(r), 0) + 1
+    tile_schedule = {"tiles_per_item_histogram": hist, "items": sum(bp.items), "ms_tuned": ms_tuned,
+                     "one_tile_per_item": {"items": items_one, "ms": ms_one},
+                     "note": "direct launches (no graph); runs tuned per (M, F, N) by ols_autotune_tiles"}
     # the same batch as one persistent launch per segment length
     bq = BatchPlan(spec.Ns, spec.M, spec.F, N=bp.N, per_n=True)
     bq.set_filters([torch.from_numpy(h).cuda() for h in hs])
@@ -421,7 +435,7 @@ def _batched(res, samples, peak):
                       "per_segment_length": {"value": outs / (ms_n * 1e-3), "ms": ms_n, "launches": n_launches,
                                              "note": "one persistent launch per distinct N, no graph"},
                       "per_signal": {"value": outs / (ms_p * 1e-3), "ms": ms_p, "launches": bp.B},
-                      "speedup_vs_per_signal": ms_p / ms_g, "total_outputs": outs}
+                      "speedup_vs_per_signal": ms_p / ms_g, "total_outputs": outs, "tile_schedule": tile_schedule}
     graph.replay()
     torch.cuda.synchronize()
     g = np.random.Generator(np.random.PCG64(5))

@@ -358,10 +358,10 @@ OLS_API int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N);
  * samples, F[b] filters of M[b] taps, segment length N[b] (N == NULL or
  * N[b] == 0: ols_autotune(M[b], F[b], flags)).  Host arrays of B entries.
  * The whole batch is ONE persistent launch: its resident blocks (N/16
- * threads for the longest N, at least 128) pull (problem, segment tile)
- * work items from an atomic ticket, the most expensive (F log2 N) first; a
- * tile is (block size x 16)/N segments of one problem, each on a slot of
- * N/16 threads with barriers of its own.  With
+ * threads for the longest N, at least 128) pull work items (runs of segment
+ * tiles of one problem, see ols_batch_plan_tiles) from an atomic ticket, the
+ * most expensive first; a tile is (block size x 16)/N segments of one
+ * problem, each on a slot of N/16 threads with barriers of its own.  With
  * OLS_BATCH_PER_N in flags, problems sharing a segment length form one
  * persistent launch each instead.  Every segment is computed exactly as by
  * ols_convolve on the same N, so results are identical to per-problem calls.
@@ -371,6 +371,39 @@ OLS_API int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N);
  */
 OLS_API int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t *M, const int32_t *F,
                            const int64_t *N, uint32_t flags);
+
+/*
+ * ols_batch_plan with the tile schedule of the single launch: an item is a
+ * run of tiles[b] consecutive tiles of problem b, taken with one ticket (the
+ * block loads the problem's twiddles once per item).  tiles == NULL or
+ * tiles[b] == 0: picked per (M, F, N) by ols_autotune_tiles with this
+ * batch's block size; a tuned run is halved while the batch has fewer than
+ * four items per resident block (the dynamic schedule needs items to balance
+ * its tail).  Items are taken most expensive first (tiles x F log2 N).
+ * Ignored with OLS_BATCH_PER_N (items of one tile).  Results do not depend
+ * on the schedule.  Errors: as ols_batch_plan; INVALID also for tiles[b] < 0.
+ */
+OLS_API int ols_batch_plan_tiles(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t *M,
+                                 const int32_t *F, const int64_t *N, const int32_t *tiles, uint32_t flags);
+
+/*
+ * Tile schedule for one problem of (M, F, N) in a single-launch batch of
+ * `block` threads (128, 256 or 512, at least N/16): the run length, in
+ * tiles per item, from {1, 2, 4, 8}.  With flags = 0 the single-launch
+ * kernel is timed on the current device for every candidate on a zero
+ * signal of about three waves of the longest items (up to ~1 GB of
+ * temporary device memory; synchronises the device) and the shortest run
+ * within 1% of the fastest per output wins; cached per (M, F, N, block) for
+ * the process.  With OLS_TUNE_MODEL: the shortest power of two giving an
+ * item ~32 transforms per slot (F + 1 per segment), at most 8.
+ * Errors: INVALID, UNSUPPORTED (N, M > N, block), ALLOC, CUDA.
+ */
+OLS_API int ols_autotune_tiles(int32_t M, int32_t F, int64_t N, int32_t block, uint32_t flags, int32_t *tiles);
+
+/* The schedule of problem b in a single-launch batch: tiles per item and
+ * number of items.  Either pointer may be NULL.  Errors: INVALID,
+ * UNSUPPORTED (an OLS_BATCH_PER_N batch). */
+OLS_API int ols_batch_schedule(ols_batch_t batch, int32_t b, int32_t *tiles, int64_t *items);
 OLS_API int ols_batch_destroy(ols_batch_t batch);
 
 /* Segment length and output length of problem b, and the number of

@@ -334,12 +334,14 @@ def autotune(M: int, F: int, model_only: bool = False) -> int:
 class BatchPlan:
     """B independent problems of uneven size (Ns[b], M[b], F[b], N[b]; N None
     or 0 entries are autotuned), convolved by one persistent launch (or, with
-    per_n, one persistent launch per distinct segment length)."""
+    per_n, one persistent launch per distinct segment length).  tiles[b]:
+    segment tiles per work item of problem b (None or 0: autotuned)."""
 
-    def __init__(self, Ns, M, F, N=None, model_only: bool = False, per_n: bool = False):
+    def __init__(self, Ns, M, F, N=None, model_only: bool = False, per_n: bool = False, tiles=None):
         flags = (_native.OLS_TUNE_MODEL if model_only else 0) | (_native.OLS_BATCH_PER_N if per_n else 0)
-        rc, handle = _native.ols_batch_plan(list(Ns), list(M), list(F), None if N is None else list(N), flags)
-        check(rc, "ols_batch_plan")
+        rc, handle = _native.ols_batch_plan_tiles(list(Ns), list(M), list(F), None if N is None else list(N),
+                                                  None if tiles is None else list(tiles), flags)
+        check(rc, "ols_batch_plan_tiles")
         self._h = handle
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.B = len(Ns)
@@ -351,6 +353,14 @@ class BatchPlan:
             self.N.append(n)
             self.Nout.append(nout)
             self.ngroups = ng
+        # single launch: tiles per item and items of every problem
+        self.tiles, self.items = [], []
+        if not per_n:
+            for b in range(self.B):
+                rc, r, n = _native.ols_batch_schedule(self._h, b)
+                check(rc, "ols_batch_schedule")
+                self.tiles.append(r)
+                self.items.append(n)
         self._keep = None
 
     def close(self):

@@ -67,6 +67,9 @@ SIGNATURES = [
     ("ols_batch_set_filters", cint, [vp, ctypes.POINTER(vp), vp]),
     ("ols_convolve_batched", cint, [vp, vp, vp, vp]),
     ("ols_batch_last_launch_count", cint, [vp]),
+    ("ols_batch_plan_tiles", cint, [ctypes.POINTER(vp), i32, P_i64, P_i32, P_i32, P_i64, P_i32, u32]),
+    ("ols_autotune_tiles", cint, [i32, i32, i64, i32, u32, P_i32]),
+    ("ols_batch_schedule", cint, [vp, i32, P_i32, P_i64]),
 ]
 
 _lib = None
@@ -225,6 +228,30 @@ def ols_batch_plan(Ns, M, F, N=None, flags: int = 0):
     h = vp()
     rc = lib().ols_batch_plan(ctypes.byref(h), B, a_ns, a_m, a_f, a_n, flags)
     return rc, h.value
+
+
+def ols_batch_plan_tiles(Ns, M, F, N=None, tiles=None, flags: int = 0):
+    B = len(Ns)
+    a_ns = (i64 * B)(*Ns)
+    a_m = (i32 * B)(*M)
+    a_f = (i32 * B)(*F)
+    a_n = (i64 * B)(*N) if N is not None else None
+    a_t = (i32 * B)(*tiles) if tiles is not None else None
+    h = vp()
+    rc = lib().ols_batch_plan_tiles(ctypes.byref(h), B, a_ns, a_m, a_f, a_n, a_t, flags)
+    return rc, h.value
+
+
+def ols_autotune_tiles(M: int, F: int, N: int, block: int, flags: int = 0):
+    r = i32()
+    rc = lib().ols_autotune_tiles(M, F, N, block, flags, ctypes.byref(r))
+    return rc, r.value
+
+
+def ols_batch_schedule(batch, b: int):
+    r, n = i32(), i64()
+    rc = lib().ols_batch_schedule(batch, b, ctypes.byref(r), ctypes.byref(n))
+    return rc, r.value, n.value
 
 
 def ols_batch_destroy(batch) -> int:

@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -28,7 +29,10 @@ struct ols_batch_s {
     std::vector<int32_t> M, F;
     std::vector<ols::BatchGroup> groups;
     ols::BatchProblemDev *d_probs = nullptr;
-    int2 *d_items = nullptr;
+    int2 *d_items = nullptr;                  // per-segment-length mode: (problem, tile)
+    int4 *d_items4 = nullptr;                 // single launch: (problem, first tile, tiles)
+    std::vector<int32_t> tiles;               // single launch: tiles per item of each problem
+    std::vector<int64_t> items_of;            // ... and the number of items of each problem
     unsigned long long *d_tickets = nullptr;
     bool filters_ready = false;
     int last_launches = 0;
@@ -134,12 +138,142 @@ double measure_per_output(int64_t N, int32_t M, int32_t F) {
     return result;
 }
 
+// ------------------------------------------------------ tile-schedule tuner
+// An item of the single-launch batch is a run of consecutive tiles of one
+// problem taken with one ticket; its length trades the per-item cost (the
+// ticket, a block barrier, the twiddle fill) against the granularity of the
+// dynamic schedule.  Candidates are 1, 2, 4 and 8 tiles per item.
+constexpr int kTileChoices[4] = {1, 2, 4, 8};
+std::map<std::tuple<int, int, int64_t, int>, int32_t> g_tiles_cache;   // (M, F, N, block) -> tiles
+
+// Model: an item should carry at least ~32 transforms per slot (F + 1 per
+// segment), so that the per-item cost stays within a few per cent.
+int32_t tiles_model(int32_t F) {
+    const int32_t want = (32 + F) / (F + 1);
+    int32_t r = 1;
+    while (r < want && r < 8) r *= 2;
+    return r;
+}
+
+// Device time per output of the single-launch kernel for one problem of
+// (M, F, N) in blocks of `block` threads, for each candidate run length, on
+// a zero signal of about three waves of the longest items (at most ~1 GB of
+// output); the shortest run within 1% of the fastest wins.  Returns 0 and
+// the choice, or a negative value on failure.
+int measure_tiles(int32_t M, int32_t F, int64_t N, int block, int sm_count, int32_t *best) {
+    const int l = log2_of(N);
+    if (block < N / 16) return -1;
+    int cap = 0;
+    if (batched_one_prepare(block, sm_count, &cap) != cudaSuccess) return -1;
+    ols_plan_t p = nullptr;
+    if (ols_plan(&p, N, M, F, OLS_FLAG_FP32) != OLS_OK) return -1;
+    const int64_t SL = (int64_t)block * 16 / N, L = N - M + 1;
+    int64_t nseg = 3ll * cap * 8 * SL;
+    const int64_t max_out = (int64_t(1) << 30) / (8ll * F);
+    if (nseg * L > max_out) nseg = std::max<int64_t>(SL, max_out / L);
+    const int64_t Nout = nseg * L, Ns = Nout + M - 1, ntiles = (nseg + SL - 1) / SL;
+    float2 *h = nullptr, *s = nullptr, *y = nullptr;
+    BatchProblemDev *dp = nullptr;
+    int4 *di = nullptr;
+    unsigned long long *tk = nullptr;
+    void **ptrs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = -1;
+    cudaError_t e = dev_alloc(&h, sizeof(float2) * (size_t)F * M);
+    if (e == cudaSuccess) e = dev_alloc(&s, sizeof(float2) * (size_t)Ns);
+    if (e == cudaSuccess) e = dev_alloc(&y, sizeof(float2) * (size_t)F * Nout);
+    if (e == cudaSuccess) e = dev_alloc(&dp, sizeof(BatchProblemDev));
+    if (e == cudaSuccess) e = dev_alloc(&di, sizeof(int4) * (size_t)ntiles);
+    if (e == cudaSuccess) e = dev_alloc(&tk, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc(&ptrs, 2 * sizeof(void *));
+    if (e == cudaSuccess) e = cudaMemset(h, 0, sizeof(float2) * (size_t)F * M);
+    if (e == cudaSuccess) e = cudaMemset(s, 0, sizeof(float2) * (size_t)Ns);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && ols_set_filters(p, reinterpret_cast<float *>(h), nullptr) != OLS_OK) e = cudaErrorUnknown;
+    BatchProblemDev d{};
+    d.Hk = reinterpret_cast<const float4 *>(p->Hk);
+    d.Ns = Ns;
+    d.Nout = Nout;
+    d.L = L;
+    d.nseg = nseg;
+    d.M = M;
+    d.F = F;
+    d.index = 0;
+    d.log2N = l;
+    void *hp[2] = {s, y};
+    if (e == cudaSuccess) e = cudaMemcpy(dp, &d, sizeof(d), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ptrs, hp, sizeof(hp), cudaMemcpyHostToDevice);
+    TwTables tw{};
+    tw.tw[l] = p->tw;
+    double t_best = 1e300, t_of[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+        const int R = kTileChoices[c];
+        std::vector<int4> items;
+        for (int64_t t0 = 0; t0 < ntiles; t0 += R)
+            items.push_back(make_int4(0, (int)t0, (int)std::min<int64_t>(R, ntiles - t0), 0));
+        e = cudaMemcpy(di, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+        const int grid = (int)std::min<int64_t>((int64_t)items.size(), cap);
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            e = cudaMemset(tk, 0, sizeof(unsigned long long));
+            if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+            if (e == cudaSuccess)
+                e = batched_one_launch(block, grid, dp, di, (long long)items.size(),
+                                       reinterpret_cast<const float2 *const *>(ptrs),
+                                       reinterpret_cast<float2 *const *>(ptrs + 1), tk, tw, nullptr);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && rep > 0) best_ms = std::min(best_ms, ms);   // rep 0 warms up
+        }
+        t_of[c] = (double)best_ms / (double)(F * Nout);
+        t_best = std::min(t_best, t_of[c]);
+    }
+    if (e == cudaSuccess) {
+        for (int c = 0; c < 4; ++c)
+            if (t_of[c] <= 1.01 * t_best) {
+                *best = kTileChoices[c];
+                rc = 0;
+                break;
+            }
+    }
+    cudaDeviceSynchronize();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (void *q : {(void *)h, (void *)s, (void *)y, (void *)dp, (void *)di, (void *)tk, (void *)ptrs})
+        if (q) cudaFree(q);
+    ols_plan_destroy(p);
+    return rc;
+}
+
+int tune_tiles(int32_t M, int32_t F, int64_t N, int block, int sm_count, uint32_t flags, int32_t *tiles) {
+    if (flags & OLS_TUNE_MODEL) {
+        *tiles = tiles_model(F);
+        return OLS_OK;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto key = std::make_tuple((int)M, (int)F, N, block);
+    auto it = g_tiles_cache.find(key);
+    if (it != g_tiles_cache.end()) {
+        *tiles = it->second;
+        return OLS_OK;
+    }
+    int32_t r = 0;
+    if (measure_tiles(M, F, N, block, sm_count, &r) != 0) return OLS_ERR_CUDA;
+    g_tiles_cache[key] = r;
+    *tiles = r;
+    return OLS_OK;
+}
+
 void free_batch(ols_batch_s *b) {
     if (!b) return;
     for (ols_plan_t p : b->plans)
         if (p) ols_plan_destroy(p);
     if (b->d_probs) cudaFree(b->d_probs);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_items4) cudaFree(b->d_items4);
     if (b->d_tickets) cudaFree(b->d_tickets);
     delete b;
 }
@@ -184,12 +318,32 @@ int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N) {
 
 int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t *M, const int32_t *F,
                    const int64_t *N, uint32_t flags) {
+    return ols_batch_plan_tiles(out, B, Ns, M, F, N, nullptr, flags);
+}
+
+int ols_autotune_tiles(int32_t M, int32_t F, int64_t N, int32_t block, uint32_t flags, int32_t *tiles) {
+    if (!tiles || M < 1 || F < 1) return OLS_ERR_INVALID;
+    const int l = log2_of(N);
+    if (l < kMinLog2N || l > kMaxLog2N || M > N) return OLS_ERR_UNSUPPORTED;
+    if ((block != 128 && block != 256 && block != 512) || block < N / 16) return OLS_ERR_UNSUPPORTED;
+    AllocScope scope;
+    int dev = 0, sms = 0;
+    if (!(flags & OLS_TUNE_MODEL)) {
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            return OLS_ERR_CUDA;
+    }
+    return tune_tiles(M, F, N, block, sms, flags, tiles);
+}
+
+int ols_batch_plan_tiles(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t *M, const int32_t *F,
+                         const int64_t *N, const int32_t *tiles, uint32_t flags) {
     AllocScope scope;
     if (!out) return OLS_ERR_INVALID;
     *out = nullptr;
     if (B < 1 || !Ns || !M || !F) return OLS_ERR_INVALID;
     for (int b = 0; b < B; ++b)
-        if (M[b] < 1 || F[b] < 1 || Ns[b] < M[b]) return OLS_ERR_INVALID;
+        if (M[b] < 1 || F[b] < 1 || Ns[b] < M[b] || (tiles && tiles[b] < 0)) return OLS_ERR_INVALID;
     ols_batch_s *bt = new (std::nothrow) ols_batch_s();
     if (!bt) return OLS_ERR_ALLOC;
     bt->B = B;
@@ -225,9 +379,8 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
         bt->N[b] = n;
     }
     if (!(flags & OLS_BATCH_PER_N)) {
-        // One persistent launch for every problem: items of 8192/N segments (one
-        // per slot of a 512-thread block), the most expensive first (an item's
-        // cost grows with F log2 N).
+        // One persistent launch for every problem: tiles of (block x 16)/N
+        // segments (one per slot of N/16 threads), items of one or more tiles.
         int cap = 0;
         int64_t maxN = 0;
         for (int b = 0; b < B; ++b) maxN = std::max<int64_t>(maxN, bt->N[b]);
@@ -255,34 +408,70 @@ int ols_batch_plan(ols_batch_t *out, int32_t B, const int64_t *Ns, const int32_t
             d.log2N = l;
             bt->tw_all.tw[l] = bt->plans[b]->tw;
         }
-        std::vector<int> order(B);
-        for (int b = 0; b < B; ++b) order[b] = b;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-            return (long long)bt->F[a] * log2_of(bt->N[a]) > (long long)bt->F[c] * log2_of(bt->N[c]);
-        });
-        std::vector<int2> items;
-        for (int b : order) {
+        // tile schedule: tiles per item of each problem, given or tuned per
+        // (M, F, N) for this block size; then, while the batch would have
+        // fewer than 4 items per resident block, runs are halved (the
+        // dynamic schedule needs items to balance the tail)
+        bt->tiles.assign(B, 1);
+        std::vector<int64_t> ntl(B);
+        for (int b = 0; b < B; ++b) {
             const int64_t sl = (int64_t)bt->one_block * 16 / bt->N[b];
-            const int64_t tiles = (bt->nseg[b] + sl - 1) / sl;
-            for (int64_t tl = 0; tl < tiles; ++tl) items.push_back(make_int2(b, (int)tl));
+            ntl[b] = (bt->nseg[b] + sl - 1) / sl;
+            int32_t r = tiles ? tiles[b] : 0;
+            if (r == 0) {
+                int rc = tune_tiles(bt->M[b], bt->F[b], bt->N[b], bt->one_block, bt->sm_count, flags, &r);
+                if (rc != OLS_OK) {
+                    free_batch(bt);
+                    return rc;
+                }
+                bt->tiles[b] = -r;          // marks a tuned choice (may be halved below)
+            } else {
+                bt->tiles[b] = r;
+            }
         }
+        auto count_items = [&]() {
+            int64_t n = 0;
+            for (int b = 0; b < B; ++b) n += (ntl[b] + std::abs(bt->tiles[b]) - 1) / std::abs(bt->tiles[b]);
+            return n;
+        };
+        for (bool shrunk = true; shrunk && count_items() < 4ll * cap;) {
+            shrunk = false;
+            for (int b = 0; b < B; ++b)
+                if (bt->tiles[b] < -1) {
+                    bt->tiles[b] /= 2;
+                    shrunk = true;
+                }
+        }
+        for (int b = 0; b < B; ++b) bt->tiles[b] = std::abs(bt->tiles[b]);
+        // items, the most expensive first: a tile's work grows with F log2 N
+        // (block x 16 points per tile whatever N), an item's with its tiles
+        std::vector<int4> items;
+        bt->items_of.assign(B, 0);
+        for (int b = 0; b < B; ++b)
+            for (int64_t t0 = 0; t0 < ntl[b]; t0 += bt->tiles[b]) {
+                items.push_back(make_int4(b, (int)t0, (int)std::min<int64_t>(bt->tiles[b], ntl[b] - t0), 0));
+                ++bt->items_of[b];
+            }
+        auto cost = [&](const int4 &it) {
+            return (long long)it.z * bt->F[it.x] * log2_of(bt->N[it.x]);
+        };
+        std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &c) { return cost(a) > cost(c); });
         BatchGroup g;
         g.log2N = 0;
         g.nitems = (long long)items.size();
         g.grid = (int)std::min<long long>(g.nitems, cap);
         e = dev_alloc(&bt->d_probs, sizeof(BatchProblemDev) * probs.size());
-        if (e == cudaSuccess) e = dev_alloc(&bt->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
+        if (e == cudaSuccess) e = dev_alloc(&bt->d_items4, sizeof(int4) * std::max<size_t>(1, items.size()));
         if (e == cudaSuccess) e = dev_alloc(&bt->d_tickets, sizeof(unsigned long long));
         if (e == cudaSuccess)
             e = cudaMemcpy(bt->d_probs, probs.data(), sizeof(BatchProblemDev) * probs.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !items.empty())
-            e = cudaMemcpy(bt->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(bt->d_items4, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             free_batch(bt);
             return status_of(e);
         }
         g.probs = bt->d_probs;
-        g.items = bt->d_items;
         g.ticket = bt->d_tickets;
         bt->groups.push_back(g);
         *out = bt;
@@ -390,7 +579,7 @@ int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_pt
     if (batch->single) {
         const BatchGroup &g = batch->groups[0];
         if (e == cudaSuccess)
-            e = batched_one_launch(batch->one_block, g.grid, g.probs, g.items, g.nitems,
+            e = batched_one_launch(batch->one_block, g.grid, g.probs, batch->d_items4, g.nitems,
                                    static_cast<const float2 *const *>(s_ptrs),
                                    static_cast<float2 *const *>(y_ptrs), g.ticket, batch->tw_all, st);
         batch->last_launches = e == cudaSuccess ? 1 : 0;
@@ -406,5 +595,13 @@ int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_pt
 }
 
 int ols_batch_last_launch_count(ols_batch_t batch) { return batch ? batch->last_launches : -1; }
+
+int ols_batch_schedule(ols_batch_t batch, int32_t b, int32_t *tiles, int64_t *items) {
+    if (!batch || b < 0 || b >= batch->B) return OLS_ERR_INVALID;
+    if (!batch->single) return OLS_ERR_UNSUPPORTED;
+    if (tiles) *tiles = batch->tiles[b];
+    if (items) *items = batch->items_of[b];
+    return OLS_OK;
+}
 
 }  // extern "C"

@@ -135,18 +135,21 @@ cudaError_t batched_launch(const BatchGroup &g, const float2 *const *s_ptrs, flo
 
 // ---------------------------------------------------------------------------
 // The whole batch in ONE persistent launch.  Blocks of 512 threads pull items
-// from one ticket; an item is SL = 512 / (N/16) consecutive segments of one
+// from one ticket; a tile is SL = 512 / (N/16) consecutive segments of one
 // problem (one per slot of N/16 threads), so every segment length fills the
 // block and needs the same shared memory (two padded exchange buffers per
 // slot: 139 KB).  The slots of an item run independently: each exchanges
 // under its own named barrier (a warp barrier when a slot is within a warp);
-// the block synchronises only to take the next item.  Each segment is
+// the block synchronises only to take the next item.  An item is a run of
+// consecutive tiles of one problem (its length, the tile schedule, is picked
+// per (M, F) by the autotuner): the block takes one ticket and loads its
+// twiddles once for the whole run.  Each segment is
 // processed exactly as by the plain kernel, so results are bitwise those of
 // per-problem calls.
 template <int BB, int LOG2N>
-__device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int tile, const float2 *const *s_ptrs,
-                                               float2 *const *y_ptrs, const float2 *tw, float2 *smem, int &xc,
-                                               uint32_t tbase) {
+__device__ __forceinline__ void batch_one_tile(const BatchProblemDev &P, int tile, bool fill,
+                                               const float2 *const *s_ptrs, float2 *const *y_ptrs, const float2 *tw,
+                                               float2 *smem, int &xc, uint32_t tbase) {
     using G = Geo<LOG2N>;
     if constexpr (G::T <= BB) {
         constexpr int SL = BB / G::T;
@@ -159,16 +162,18 @@ __device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int til
 #if OLS_FWD_TW_TMEM
         // the same TMEM layout as the plain kernel (twiddles of this N, then the
         // segment spectrum), so results stay bitwise those of per-problem calls
-        // (the TMEM exchange at the segment lengths of OLS_BATCH_TX_MASK)
+        // (the TMEM exchange at the segment lengths of OLS_BATCH_TX_MASK); the
+        // twiddles are written on an item's first tile only
         constexpr bool xch = in_tx_mask<LOG2N>(OLS_BATCH_TX_MASK);
         using TWT = TwTmemT<xch>;
         const TWT twt{tbase + tmem::lane_bits() + (uint32_t)(threadIdx.x / 128) * 128u};
-        tw_tmem_fill<LOG2N, xch>(tw, twt.base, t);
+        if (fill) tw_tmem_fill<LOG2N, xch>(tw, twt.base, t);
         ols_segment<LOG2N, TWT, true, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, twt, y_ptrs[P.index],
                                                                P.M, P.F, P.L, P.Nout, seg, seg < P.nseg, bufs, t, xc,
                                                                0u, bar);
 #else
         (void)tbase;
+        (void)fill;
         ols_segment<LOG2N, TwGlobal, false, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, TwGlobal{tw},
                                                                   y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
                                                                   seg < P.nseg, bufs, t, xc, 0u, bar);
@@ -178,7 +183,7 @@ __device__ __forceinline__ void batch_one_item(const BatchProblemDev &P, int til
 
 template <int BB>
 __global__ void __launch_bounds__(BB, kBatchOneBlock / BB)
-ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__restrict__ items, long long nitems,
+ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int4 *__restrict__ items, long long nitems,
                        const float2 *const *__restrict__ s_ptrs, float2 *const *__restrict__ y_ptrs,
                        unsigned long long *__restrict__ ticket, TwTables tw) {
     extern __shared__ float4 smem_raw[];
@@ -195,24 +200,39 @@ ols_batched_one_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__
     tbase = 0;
 #endif
     int xc = 0;
+    // One tile per iteration.  An item's tiles run one after another (a slot
+    // takes segment `slot` of each tile without synchronising with the other
+    // slots); the block synchronises only to take the next item.  Only the
+    // item index and the tiles left stay live across tiles: the item and its
+    // problem are read again for every tile (cache hits), which keeps the
+    // tile body at the register budget of one-tile items.
+    long long item = 0;
+    int r = 0, left = 0;
     for (;;) {
-        __syncthreads();                       // every slot is done with the previous item
-        if (threadIdx.x == 0) item_sh = (long long)atomicAdd(ticket, 1ull);
-        __syncthreads();
-        const long long item = item_sh;
-        if (item >= nitems) break;
-        const int2 it = items[item];           // (problem, tile)
+        if (left == 0) {
+            __syncthreads();                   // every slot is done with the previous item
+            if (threadIdx.x == 0) item_sh = (long long)atomicAdd(ticket, 1ull);
+            __syncthreads();
+            item = item_sh;
+            if (item >= nitems) break;
+            left = items[item].z;
+            r = 0;
+            xc = 0;                            // buffers restart with every item
+        }
+        const int4 it = items[item];           // (problem, first tile, tiles)
         const BatchProblemDev P = probs[it.x];
-        xc = 0;                                // buffers restart with every item
+        const int tile = it.y + r;
         switch (P.log2N) {
-            case 8: batch_one_item<BB, 8>(P, it.y, s_ptrs, y_ptrs, tw.tw[8], smem, xc, tbase); break;
-            case 9: batch_one_item<BB, 9>(P, it.y, s_ptrs, y_ptrs, tw.tw[9], smem, xc, tbase); break;
-            case 10: batch_one_item<BB, 10>(P, it.y, s_ptrs, y_ptrs, tw.tw[10], smem, xc, tbase); break;
-            case 11: batch_one_item<BB, 11>(P, it.y, s_ptrs, y_ptrs, tw.tw[11], smem, xc, tbase); break;
-            case 12: batch_one_item<BB, 12>(P, it.y, s_ptrs, y_ptrs, tw.tw[12], smem, xc, tbase); break;
-            case 13: batch_one_item<BB, 13>(P, it.y, s_ptrs, y_ptrs, tw.tw[13], smem, xc, tbase); break;
+            case 8: batch_one_tile<BB, 8>(P, tile, r == 0, s_ptrs, y_ptrs, tw.tw[8], smem, xc, tbase); break;
+            case 9: batch_one_tile<BB, 9>(P, tile, r == 0, s_ptrs, y_ptrs, tw.tw[9], smem, xc, tbase); break;
+            case 10: batch_one_tile<BB, 10>(P, tile, r == 0, s_ptrs, y_ptrs, tw.tw[10], smem, xc, tbase); break;
+            case 11: batch_one_tile<BB, 11>(P, tile, r == 0, s_ptrs, y_ptrs, tw.tw[11], smem, xc, tbase); break;
+            case 12: batch_one_tile<BB, 12>(P, tile, r == 0, s_ptrs, y_ptrs, tw.tw[12], smem, xc, tbase); break;
+            case 13: batch_one_tile<BB, 13>(P, tile, r == 0, s_ptrs, y_ptrs, tw.tw[13], smem, xc, tbase); break;
             default: break;
         }
+        ++r;
+        --left;
     }
 #if OLS_FWD_TW_TMEM
     tmem::fence_before_sync();
@@ -250,7 +270,7 @@ cudaError_t batched_one_prepare(int block, int sm_count, int *grid_cap) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
+cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int4 *items, long long nitems,
                                const float2 *const *s_ptrs, float2 *const *y_ptrs, unsigned long long *ticket,
                                const TwTables &tw, cudaStream_t st) {
     if (block == 128)

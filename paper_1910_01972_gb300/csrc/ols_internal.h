@@ -151,11 +151,12 @@ struct TwTables {
 };
 
 // The whole batch in one persistent launch: blocks of `block` threads (the
-// longest segment's N/16, at least 128); an item is block * 16 / N consecutive
-// segments of one problem (one per N/16-thread slot).
+// longest segment's N/16, at least 128); a tile is block * 16 / N consecutive
+// segments of one problem (one per N/16-thread slot), and an item (problem,
+// first tile, tiles) a run of consecutive tiles taken with one ticket.
 constexpr int kBatchOneBlock = 512;   // largest block (N = 8192 needs 512 threads)
 cudaError_t batched_one_prepare(int block, int sm_count, int *grid_cap);
-cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int2 *items, long long nitems,
+cudaError_t batched_one_launch(int block, int grid, const BatchProblemDev *probs, const int4 *items, long long nitems,
                                const float2 *const *s_ptrs, float2 *const *y_ptrs, unsigned long long *ticket,
                                const TwTables &tw, cudaStream_t st);
 

@@ -163,3 +163,53 @@ def test_single_launch_block_sizes_cover_every_segment_length():
             p.close()
             assert oracle.max_stream_rel_l2(ys[b].cpu().numpy(), oracle.conv(ss[b], hs[b])) <= TOL
         bp.close()
+
+
+@pytest.mark.parametrize("tiles", [[1] * 7, [3, 1, 2, 8, 5, 4, 7], [8] * 7])
+def test_tile_schedules_give_identical_results(tiles):
+    """The single launch's items as runs of 1 to 8 tiles (every run length,
+    ragged last runs): outputs bit for bit those of per-problem calls."""
+    ss, hs = small_inputs(5)
+    sd = [dev(s) for s in ss]
+    bp = BatchPlan(SMALL["Ns"], SMALL["M"], SMALL["F"], SMALL["N"], tiles=tiles)
+    assert bp.tiles == tiles
+    bp.set_filters([dev(h) for h in hs])
+    ys = bp.convolve(sd)
+    torch.cuda.synchronize()
+    block = max(128, max(SMALL["N"]) // 16)
+    for b in range(bp.B):
+        seg_per_tile = block * 16 // SMALL["N"][b]
+        nseg = -(-(SMALL["Ns"][b] - SMALL["M"][b] + 1) // (SMALL["N"][b] - SMALL["M"][b] + 1))
+        ntiles = -(-nseg // seg_per_tile)
+        assert bp.items[b] == -(-ntiles // tiles[b])
+        p = Plan(SMALL["M"][b], SMALL["F"][b], SMALL["N"][b])
+        p.set_filters(dev(hs[b]))
+        assert torch.equal(ys[b], p.convolve(sd[b])), b
+        p.close()
+    bp.close()
+
+
+def test_tile_schedule_autotuned():
+    """Tuned runs are powers of two up to 8, cached, and the tuned batch
+    matches the oracle; the model choice follows its stated rule."""
+    from paper_1910_01972_gb300 import _native
+    for F in (1, 8, 40):
+        rc, r = _native.ols_autotune_tiles(129, F, 1024, 256, 0)
+        assert rc == _native.OLS_OK and r in (1, 2, 4, 8)
+        rc2, r2 = _native.ols_autotune_tiles(129, F, 1024, 256, 0)
+        assert rc2 == _native.OLS_OK and r2 == r
+        rc, rm = _native.ols_autotune_tiles(129, F, 1024, 256, _native.OLS_TUNE_MODEL)
+        want = max(1, -(-32 // (F + 1)))
+        expect = 1
+        while expect < want and expect < 8:
+            expect *= 2
+        assert rm == expect
+    assert _native.ols_autotune_tiles(129, 4, 8192, 256, 0)[0] == _native.OLS_ERR_UNSUPPORTED   # block < N/16
+    ss, hs = small_inputs(6)
+    bp = BatchPlan(SMALL["Ns"], SMALL["M"], SMALL["F"], SMALL["N"])
+    assert all(r in (1, 2, 4, 8) for r in bp.tiles)
+    bp.set_filters([dev(h) for h in hs])
+    ys = bp.convolve([dev(s) for s in ss])
+    for b in range(bp.B):
+        assert oracle.max_stream_rel_l2(ys[b].cpu().numpy(), oracle.conv(ss[b], hs[b])) <= TOL
+    bp.close()
