@@ -780,16 +780,20 @@ def run_ours(args):
         h2d = 8 * (cfg.Ns + (cseg_chunks - 1) * (cfg.M - 1))
         # the host link on this machine, same run: one whole-array copy each way
         # (pinned), the floor of any pipelined host-buffer convolution
+        # (the best of three individually timed copies: one copy of 2 GB is
+        # itself noisy from call to call)
         link = {}
         for name, dst, src in (("h2d", s, s_host), ("d2h", y_host, y)):
             dst.copy_(src, non_blocking=True)
             torch.cuda.synchronize()
-            e0.record(st)
+            times = []
             for _ in range(3):
+                e0.record(st)
                 dst.copy_(src, non_blocking=True)
-            e1.record(st)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / 3
+                e1.record(st)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = min(times)
             link[name + "_GBps"] = src.numel() * 8 / (ms * 1e-3) / 1e9
             link[name + "_ms"] = ms
         link["floor_ms"] = max(link["h2d_ms"], link["d2h_ms"])
