@@ -505,7 +505,7 @@ def _tensor_core(res, samples, peak, ns=0):
 
 
 def _r2r(res, samples, peak, ns=0):
-    """Real-to-real form (Sec. 3.3's R2R variant) on the filter-bank shape
+    """Real-to-real form (Sec. 3.4's R2R variant) on the filter-bank shape
     (`ns` overrides the signal length)."""
     import dataclasses
     import numpy as np
@@ -589,7 +589,7 @@ def _post(res, samples, peak):
 
 def _cufft_ols(res, samples, peak):
     """Library comparison, not the product path: the unfused overlap-and-save of
-    Sec. 3.2 with cuFFT through torch.fft (segment separation, batched forward
+    Sec. 3.3 with cuFFT through torch.fft (segment separation, batched forward
     FFT, product with every filter's spectrum, batched inverse FFT, discard of
     the M-1 aliased samples), each step a separate kernel with its result in
     HBM.  The paper's cuFFT-OLS uses load/store callbacks for the product and

@@ -88,7 +88,7 @@ typedef struct ols_batch_s *ols_batch_t;
  * overflow).  Forward convolution only (ols_convolve, ols_convolve_host). */
 #define OLS_FLAG_TC_FP16SPLIT 1u
 #define OLS_FLAG_TC_BF16SPLIT 2u
-/* Real-to-real convolution (Sec. 3.3's R2R variant and Algorithm 2 with
+/* Real-to-real convolution (Sec. 3.4's R2R variant and Algorithm 2 with
  * real input): real signal, F real filters, real outputs, FP32.  Such a plan
  * serves only ols_set_filters_real / ols_convolve_real (and the host-side
  * queries); the complex entry points return OLS_ERR_UNSUPPORTED for it. */
@@ -113,7 +113,7 @@ OLS_API int ols_geometry(int64_t N, int32_t M, int64_t Ns, int64_t *L, int64_t *
 
 /*
  * The library's internal spectral order -- pure host, needs no GPU.
- * Sec. 3.3 notes that the point-wise product does not care about the order
+ * Sec. 3.4 notes that the point-wise product does not care about the order
  * of the spectrum as long as signal and filter share it and the inverse
  * transform consumes it, so the forward FFT skips the reordering step.  This
  * returns, for each storage position q in [0, N), the frequency index
@@ -162,7 +162,7 @@ OLS_API int ols_set_filters(ols_plan_t plan, const float *h, void *stream);
 OLS_API int ols_get_spectra(ols_plan_t plan, float *H, void *stream);
 
 /*
- * The fused OLS convolution (Algorithm 2, Sec. 3.3): one kernel; each
+ * The fused OLS convolution (Algorithm 2, Sec. 3.4): one kernel; each
  * segment of s is read from HBM once, forward-transformed in registers and
  * shared memory, and for every filter multiplied by its spectrum, inverse
  * transformed, stripped of its M-1 aliased samples and written once.
@@ -178,7 +178,7 @@ OLS_API int ols_convolve(ols_plan_t plan, const float *s, int64_t Ns, float *y, 
  * split: every sample x = (x_hi + x_lo), each part a pair of 16-bit numbers
  * (Re, Im) in the plan's 16-bit type (FP16 or BF16).  The paper has no
  * split storage; it is the input form of the split-precision convolution
- * (the tensor-core MMAs take 16-bit operands, Sec. 3.3's FFT stages as
+ * (the tensor-core MMAs take 16-bit operands, Sec. 3.4's FFT stages as
  * matrix products), 8 bytes per sample like FP32.
  * s_hi, s_lo: device [Ns] planes of 32-bit words, each word one sample's
  * (Re, Im) pair, Re in the low half (4-byte aligned).  y: device
@@ -214,7 +214,7 @@ OLS_API int ols_split_signal(ols_plan_t plan, const float *s, int64_t Ns, void *
 OLS_API int ols_set_filters_real(ols_plan_t plan, const float *h, void *stream);
 
 /*
- * Real-to-real fused OLS convolution (Sec. 3.3's R2R variant; Eq. 1 on real
+ * Real-to-real fused OLS convolution (Sec. 3.4's R2R variant; Eq. 1 on real
  * data, valid part):  y_f[j] = sum_k s[j+M-1-k] h_f[k],  j < Ns-M+1.
  * s: device [Ns] real FP32; y: device [F][Ns-M+1] real FP32 (row f = filter
  * f); both 4-byte aligned, not overlapping.  One kernel: each segment of s is

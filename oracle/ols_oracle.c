@@ -31,7 +31,7 @@
  *
  * where g_f[j] = dL/dRe y_f[j] + i dL/dIm y_f[j].
  *
- * The paper's second variant (Sec. 3.3, the R2R SM-OLS) convolves a real
+ * The paper's second variant (Sec. 3.4, the R2R SM-OLS) convolves a real
  * signal with real filters; its exact result is the same valid part of Eq. 1
  * on real data, computed here separately in real FP64 (ols_oracle_conv_real).
  *
@@ -187,7 +187,7 @@ static double conv_one_real(const float *s, int32_t M, const float *hf, int64_t 
 
 /*
  * Real-to-real valid-mode convolution for a bank of F filters (Eq. 1 on real
- * data, the R2R form of Sec. 3.3).  s: [Ns] real (FP32), h: [F][M] real
+ * data, the R2R form of Sec. 3.4).  s: [Ns] real (FP32), h: [F][M] real
  * (FP32), y: [F][Ns-M+1] real (FP64).  Returns 0, or -1 on invalid sizes.
  */
 int ols_oracle_conv_real(int64_t Ns, const float *s, int32_t M, int32_t F,

@@ -1,6 +1,6 @@
 // fft_regs.cuh -- register-resident DFT building blocks for the OLS kernels.
 //
-// Sec. 3.3 of the paper computes each segment's FFT inside the convolution
+// Sec. 3.4 of the paper computes each segment's FFT inside the convolution
 // kernel ("device-callable" FFTs on data held in shared memory and
 // registers).  These are the in-register pieces: small DFTs of 2, 4, 8 and 16
 // points on a thread's own values, with every internal rotation a

@@ -6,7 +6,7 @@
 // stride 1, exchanging between passes through shared memory or, for the last
 // exchange of kernels with TMEM twiddles (N = 512 .. 4096), through TMEM.
 // * forward passes: decimation in frequency, natural-order input, spectrum
-//   left in mixed-radix digit-reversed order (no reordering step: Sec. 3.3
+//   left in mixed-radix digit-reversed order (no reordering step: Sec. 3.4
 //   notes the order is irrelevant to a point-wise product as long as both
 //   operands and the inverse transform share it);
 // * inverse passes: the exact reverse (decimation in time), digit-reversed

@@ -1,8 +1,8 @@
 // ols_forward.cu -- the fused overlap-and-save convolution kernel (FP32).
 //
-// Algorithm 2 / Sec. 3.3 of the paper: one kernel; a thread-block owns a
+// Algorithm 2 / Sec. 3.4 of the paper: one kernel; a thread-block owns a
 // segment; the segment's forward FFT is done on chip and its spectrum kept
-// on chip (Sec. 3.3 keeps it in registers), then for every filter: point-wise
+// on chip (Sec. 3.4 keeps it in registers), then for every filter: point-wise
 // product with the filter's precomputed spectrum, inverse FFT, removal of
 // the M-1 aliased samples, store (Sec. 3.2).
 //
@@ -13,7 +13,7 @@
 //   2/4/8/16 at stride 1.
 // * Forward: decimation in frequency, natural-order input, digit-reversed
 //   spectrum.  Inverse: the exact reverse of the passes (decimation in time),
-//   digit-reversed input, natural-order output.  No reordering step (Sec. 3.3
+//   digit-reversed input, natural-order output.  No reordering step (Sec. 3.4
 //   notes the order is irrelevant to the point-wise product).
 // * Tensor memory holds, in each thread's own lane, its pass twiddles and the
 //   segment spectrum (read back once per filter), and stages the exchange

@@ -1,5 +1,5 @@
 // ols_r2r.cu -- the fused overlap-and-save convolution of a REAL signal with
-// a bank of REAL filters (the paper's R2R variant, Sec. 3.3 and Algorithm 2).
+// a bank of REAL filters (the paper's R2R variant, Sec. 3.4 and Algorithm 2).
 //
 // The paper runs its R2R kernel on half-length complex FFTs (Stockham
 // autosort, with real-to-complex and complex-to-real post-processing).  Here

@@ -104,7 +104,7 @@ DIFF = Plain("diff_Ns4194304_F16_M129_N1024", 1 << 22, 16, 129, 1024, False, 3)
 TC_SPLIT = Plain("tc_Ns16777216_F64_M512_N4096", 1 << 24, 64, 512, 4096, False, 4)
 
 
-# real-to-real form (Sec. 3.3's R2R variant) on the filter-bank shape
+# real-to-real form (Sec. 3.4's R2R variant) on the filter-bank shape
 R2R_BANK = Plain("r2r_bank_Ns8388608_F32_M257_N2048", 1 << 23, 32, 257, 2048, True, 5)
 
 

@@ -252,7 +252,7 @@ QUICK_PINS = (pin_golden_conv, pin_golden_adjoint, pin_bruteforce_dft, pin_delta
 
 
 # ------------------------------------------------------ real-to-real (R2R) form
-# The paper's second OLS variant (Sec. 3.3) convolves real signals with real
+# The paper's second OLS variant (Sec. 3.4) convolves real signals with real
 # filters; its exact result is Eq. 1's valid part on real data.  Each pin
 # takes conv_real(s, h) -> y (float64) on float32 inputs.
 

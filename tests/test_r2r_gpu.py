@@ -1,4 +1,4 @@
-"""Parity of the real-to-real fused OLS kernel (Sec. 3.3's R2R variant, through
+"""Parity of the real-to-real fused OLS kernel (Sec. 3.4's R2R variant, through
 the C ABI) with the FP64 real oracle.
 
 Tolerance: max over filters of ||y - y_ref||_2 / ||y_ref||_2 <= 2e-6, the
