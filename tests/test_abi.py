@@ -110,3 +110,21 @@ def test_null_handles_are_rejected():
     assert L.ols_set_filters(None, None, None) == _native.OLS_ERR_INVALID
     assert L.ols_plan_destroy(None) == 0
     assert L.ols_last_launch_count(None) == -1
+
+
+def test_tile_schedule_model_rule_and_argument_checks():
+    """ols_autotune_tiles with OLS_TUNE_MODEL is host arithmetic: the shortest
+    power of two giving an item ~32 transforms per slot (F + 1 per segment),
+    at most 8; invalid sizes are refused before any device call."""
+    for F in (1, 2, 3, 7, 8, 15, 16, 31, 32, 128):
+        rc, r = _native.ols_autotune_tiles(129, F, 1024, 256, _native.OLS_TUNE_MODEL)
+        assert rc == _native.OLS_OK
+        want = -(-32 // (F + 1))
+        assert r in (1, 2, 4, 8) and (r >= want or r == 8) and (r == 1 or r // 2 < want), (F, r)
+    U, I = _native.OLS_ERR_UNSUPPORTED, _native.OLS_ERR_INVALID
+    assert _native.ols_autotune_tiles(129, 4, 1000, 256, _native.OLS_TUNE_MODEL)[0] == U    # N not a power of two
+    assert _native.ols_autotune_tiles(2000, 4, 1024, 256, _native.OLS_TUNE_MODEL)[0] == U   # M > N
+    assert _native.ols_autotune_tiles(129, 4, 8192, 256, _native.OLS_TUNE_MODEL)[0] == U    # block < N / 16
+    assert _native.ols_autotune_tiles(129, 4, 1024, 384, _native.OLS_TUNE_MODEL)[0] == U    # block size
+    assert _native.ols_autotune_tiles(0, 4, 1024, 256, _native.OLS_TUNE_MODEL)[0] == I
+    assert _native.ols_autotune_tiles(129, 0, 1024, 256, _native.OLS_TUNE_MODEL)[0] == I
