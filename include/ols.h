@@ -349,7 +349,7 @@ OLS_API int ols_convolve_backward(ols_plan_t plan, const float *s, int64_t Ns, c
  * fastest per output sample wins; results are cached per (M, F) for the
  * process and, if the environment variable OLS_AUTOTUNE_CACHE names a file,
  * read from and appended to it ("M F N" lines).  With OLS_TUNE_MODEL, no
- * measurement.  Errors: INVALID, UNSUPPORTED (M > 8192), CUDA.
+ * measurement.  Errors: INVALID, UNSUPPORTED (M > 8192), ALLOC, CUDA.
  */
 OLS_API int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N);
 

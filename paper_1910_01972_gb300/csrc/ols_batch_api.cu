@@ -90,10 +90,12 @@ void store_tune_file_locked(int M, int F, int64_t N) {
 
 // Device time per output sample of the fused kernel for (N, M, F), on a
 // zero signal of about two waves of segments (timing does not depend on the
-// values).  Returns a negative value on failure.
-double measure_per_output(int64_t N, int32_t M, int32_t F) {
+// values), into *t.  Returns an ols_status (an allocation failure stays
+// OLS_ERR_ALLOC).
+int measure_per_output(int64_t N, int32_t M, int32_t F, double *t) {
     ols_plan_t p = nullptr;
-    if (ols_plan(&p, N, M, F, OLS_FLAG_FP32) != OLS_OK) return -1.0;
+    int rc = ols_plan(&p, N, M, F, OLS_FLAG_FP32);
+    if (rc != OLS_OK) return rc;
     double result = -1.0;
     float2 *h = nullptr, *s = nullptr, *y = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -128,6 +130,8 @@ double measure_per_output(int64_t N, int32_t M, int32_t F) {
         }
         if (ok) result = (double)best * 1e-3 / (double)(F * Nout);
     }
+    rc = e != cudaSuccess ? status_of(e) : (result < 0 ? OLS_ERR_CUDA : OLS_OK);
+    *t = result;
     cudaDeviceSynchronize();
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -135,7 +139,7 @@ double measure_per_output(int64_t N, int32_t M, int32_t F) {
     if (s) cudaFree(s);
     if (y) cudaFree(y);
     ols_plan_destroy(p);
-    return result;
+    return rc;
 }
 
 // ------------------------------------------------------ tile-schedule tuner
@@ -158,15 +162,17 @@ int32_t tiles_model(int32_t F) {
 // Device time per output of the single-launch kernel for one problem of
 // (M, F, N) in blocks of `block` threads, for each candidate run length, on
 // a zero signal of about three waves of the longest items (at most ~1 GB of
-// output); the shortest run within 1% of the fastest wins.  Returns 0 and
-// the choice, or a negative value on failure.
+// output); the shortest run within 1% of the fastest wins.  Returns an
+// ols_status (an allocation failure stays OLS_ERR_ALLOC) and the choice.
 int measure_tiles(int32_t M, int32_t F, int64_t N, int block, int sm_count, int32_t *best) {
     const int l = log2_of(N);
-    if (block < N / 16) return -1;
+    if (block < N / 16) return OLS_ERR_UNSUPPORTED;
     int cap = 0;
-    if (batched_one_prepare(block, sm_count, &cap) != cudaSuccess) return -1;
+    cudaError_t e0p = batched_one_prepare(block, sm_count, &cap);
+    if (e0p != cudaSuccess) return status_of(e0p);
     ols_plan_t p = nullptr;
-    if (ols_plan(&p, N, M, F, OLS_FLAG_FP32) != OLS_OK) return -1;
+    int prc = ols_plan(&p, N, M, F, OLS_FLAG_FP32);
+    if (prc != OLS_OK) return prc;
     const int64_t SL = (int64_t)block * 16 / N, L = N - M + 1;
     int64_t nseg = 3ll * cap * 8 * SL;
     const int64_t max_out = (int64_t(1) << 30) / (8ll * F);
@@ -178,7 +184,7 @@ int measure_tiles(int32_t M, int32_t F, int64_t N, int block, int sm_count, int3
     unsigned long long *tk = nullptr;
     void **ptrs = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int rc = -1;
+    int rc = OLS_ERR_CUDA;
     cudaError_t e = dev_alloc(&h, sizeof(float2) * (size_t)F * M);
     if (e == cudaSuccess) e = dev_alloc(&s, sizeof(float2) * (size_t)Ns);
     if (e == cudaSuccess) e = dev_alloc(&y, sizeof(float2) * (size_t)F * Nout);
@@ -235,9 +241,11 @@ int measure_tiles(int32_t M, int32_t F, int64_t N, int block, int sm_count, int3
         for (int c = 0; c < 4; ++c)
             if (t_of[c] <= 1.01 * t_best) {
                 *best = kTileChoices[c];
-                rc = 0;
+                rc = OLS_OK;
                 break;
             }
+    } else {
+        rc = status_of(e);
     }
     cudaDeviceSynchronize();
     if (e0) cudaEventDestroy(e0);
@@ -261,7 +269,8 @@ int tune_tiles(int32_t M, int32_t F, int64_t N, int block, int sm_count, uint32_
         return OLS_OK;
     }
     int32_t r = 0;
-    if (measure_tiles(M, F, N, block, sm_count, &r) != 0) return OLS_ERR_CUDA;
+    const int rc = measure_tiles(M, F, N, block, sm_count, &r);
+    if (rc != OLS_OK) return rc;
     g_tiles_cache[key] = r;
     *tiles = r;
     return OLS_OK;
@@ -302,8 +311,9 @@ int ols_autotune(int32_t M, int32_t F, uint32_t flags, int64_t *N) {
         const int64_t n = int64_t(1) << l;
         if (M > n) continue;
         if ((n - M + 1) * 16 < n && n != (int64_t(1) << kMaxLog2N)) continue;   // < 1/16 of each FFT kept
-        const double t = measure_per_output(n, M, F);
-        if (t < 0) return OLS_ERR_CUDA;
+        double t = -1.0;
+        const int rc = measure_per_output(n, M, F, &t);
+        if (rc != OLS_OK) return rc;
         if (t < best) {
             best = t;
             bestN = n;

@@ -77,22 +77,47 @@ def test_plan_allocation_failure_at_every_step(env):
     plan.close()
 
 
-def test_batch_plan_allocation_failure(env):
+def _batch_until_success(env, make, limit=400):
+    """Fail allocation k = 1, 2, ... of one batch-plan call until it succeeds;
+    every failed call must report OLS_ERR_ALLOC.  Returns the failures seen."""
     lib = _native.lib()
+    for k in range(1, limit):
+        env["OLS_FAIL_ALLOC"] = str(k)
+        b = ctypes.c_void_p()
+        rc = make(lib, b)
+        if rc == _native.OLS_OK:
+            env.pop("OLS_FAIL_ALLOC")
+            assert lib.ols_batch_destroy(b) == _native.OLS_OK
+            return k - 1
+        assert rc == _native.OLS_ERR_ALLOC, (k, _native.ols_status_string(rc))
+        assert not b.value
+    raise AssertionError("no success within %d allocations" % limit)
+
+
+def test_batch_plan_allocation_failure(env):
+    """Every allocation of a batch plan, including those of the autotuners'
+    timing runs (segment length, tile schedule), fails cleanly."""
     Ns = (ctypes.c_int64 * 3)(20_000, 30_000, 9_000)
     M = (ctypes.c_int32 * 3)(33, 65, 129)
     F = (ctypes.c_int32 * 3)(4, 2, 3)
     N = (ctypes.c_int64 * 3)(512, 1024, 1024)
-    for k in (1, 4, 9, 19, 21):       # 6 per FP32 plan, then the batch tables
-        env["OLS_FAIL_ALLOC"] = str(k)
-        b = ctypes.c_void_p()
-        rc = lib.ols_batch_plan(ctypes.byref(b), 3, Ns, M, F, N, 0)
-        assert rc == _native.OLS_ERR_ALLOC, (k, _native.ols_status_string(rc))
-        assert not b.value
-    env.pop("OLS_FAIL_ALLOC")
-    b = ctypes.c_void_p()
-    assert lib.ols_batch_plan(ctypes.byref(b), 3, Ns, M, F, N, 0) == _native.OLS_OK
-    assert lib.ols_batch_destroy(b) == _native.OLS_OK
+    one = (ctypes.c_int32 * 3)(1, 1, 1)
+    base = _free_bytes()
+    # given N and tiles: 6 allocations per FP32 plan, then 3 batch tables
+    n = _batch_until_success(env, lambda lib, b: lib.ols_batch_plan_tiles(ctypes.byref(b), 3, Ns, M, F, N, one, 0))
+    assert n == 3 * 6 + 3
+    # tuned tile schedule (shapes no other test tunes): the tuner's timing runs allocate too
+    Mt = (ctypes.c_int32 * 3)(35, 67, 131)
+    Ft = (ctypes.c_int32 * 3)(5, 3, 7)
+    n = _batch_until_success(env, lambda lib, b: lib.ols_batch_plan(ctypes.byref(b), 3, Ns, Mt, Ft, N, 0))
+    assert n > 3 * 6 + 3
+    # tuned segment length (an (M, F) no other test tunes): its timing runs too
+    Ns1 = (ctypes.c_int64 * 1)(40_000)
+    M1 = (ctypes.c_int32 * 1)(77)
+    F1 = (ctypes.c_int32 * 1)(3)
+    n = _batch_until_success(env, lambda lib, b: lib.ols_batch_plan(ctypes.byref(b), 1, Ns1, M1, F1, None, 0))
+    assert n > 6 + 3
+    assert abs(_free_bytes() - base) < (8 << 20)
 
 
 def test_host_pipeline_allocation_failure(env):

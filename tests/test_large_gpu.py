@@ -1,7 +1,9 @@
 """Maximum sizes: a signal of more than 2^31 samples (outputs past the 32-bit
-index range) through the fused complex kernel and the real-to-real kernel,
-checked at sampled outputs against the FP64 oracle (tolerance 2e-6 relative
-L2, the FP32 bar).  The signal is drawn on the device (17 GB complex, 8.6 GB
+index range) through the fused complex kernel, the real-to-real kernel, the
+post-processing kernels, the tensor-core kernel (FP32 and split-plane input)
+and the adjoint, checked at sampled outputs against the FP64 oracle
+(tolerance 2e-6 relative L2, the FP32 bar; the tensor-core form's FP16 bound
+is the same).  The signal is drawn on the device (17 GB complex, 8.6 GB
 real); each sampled output's M-sample input window is gathered and given to
 the oracle."""
 import numpy as np
@@ -129,4 +131,96 @@ def test_power_and_derivative_beyond_2_to_31():
     assert np.linalg.norm(got_d - ref_d) / np.linalg.norm(ref_y) <= TOL
     plan.close()
     del s
+    torch.cuda.empty_cache()
+
+
+def test_tensor_core_split_beyond_2_to_31():
+    """The FP16 split tensor-core kernel at the same size, from the FP32
+    signal and from its split planes (equal bit for bit)."""
+    M, F, N = 64, 1, 512
+    g = np.random.Generator(np.random.PCG64(80))
+    h = synth.filters(g, F, M)
+    s = synth.device_signal(NS, seed=504)
+    plan = Plan(M, F, N, flags=_native.OLS_FLAG_TC_FP16SPLIT)
+    plan.set_filters(torch.from_numpy(h).cuda())
+    y = plan.convolve(s)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    q = plan.query(NS)
+    Nout, L = q["Nout"], q["L"]
+    j = _sample_outputs(Nout, L, 9)
+    got = y[0, torch.from_numpy(j).cuda()].cpu().numpy()
+    win = _windows(s, j, M)
+    ref = np.array([oracle.conv_at(win[i], h, [0], [0])[0] for i in range(len(j))])
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL
+    hi, lo = plan.split_signal(s)
+    del s
+    y2 = plan.convolve_split(hi, lo)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.equal(y, y2)
+    plan.close()
+    del y, y2, hi, lo
+    torch.cuda.empty_cache()
+
+
+def test_adjoint_beyond_2_to_31():
+    """The adjoint with an output gradient that is zero except at a few
+    outputs, some past 2^31 and at segment boundaries there: ds near each
+    nonzero gradient entry and dh (a sum over all 2^31 outputs) against the
+    oracle's adjoint of local windows, one per cluster of entries (clusters
+    are > 2M apart, so each local window sees all the entries that reach
+    it)."""
+    M, F, N = 64, 2, 512
+    rng = np.random.Generator(np.random.PCG64(81))
+    h = synth.filters(rng, F, M)
+    s = synth.device_signal(NS, seed=505)
+    plan = Plan(M, F, N)
+    plan.set_filters(torch.from_numpy(h).cuda())
+    q = plan.query(NS)
+    Nout, L = q["Nout"], q["L"]
+    b31 = 1 << 31
+    seg31 = (b31 // L) * L
+    support = [(0, 3), (1, 5000), (0, seg31 - 1), (1, seg31), (0, b31 - 1), (1, b31 + 700), (0, Nout - 1)]
+    vals = (rng.normal(size=len(support)) + 1j * rng.normal(size=len(support))).astype(np.complex64)
+    gy = torch.zeros((F, Nout), dtype=torch.complex64, device="cuda")
+    for (f, j0), v in zip(support, vals):
+        gy[f, j0] = complex(v)
+    ds, dh = plan.convolve_backward(s, gy)
+    torch.cuda.synchronize()
+    del gy
+    dh_ref = np.zeros((F, M), np.complex128)
+    got, want = [], []
+    # entries closer than 2M (the segment boundary pair) share one local window
+    order = sorted(range(len(support)), key=lambda i: support[i][1])
+    clusters = []
+    for i in order:
+        if clusters and support[i][1] - support[clusters[-1][-1]][1] <= 2 * M:
+            clusters[-1].append(i)
+        else:
+            clusters.append([i])
+    for cl in clusters:
+        jmin, jmax = support[cl[0]][1], support[cl[-1]][1]
+        a = max(0, jmin - (M - 1))
+        nl = min(Nout, jmax + M) - a                   # local outputs [a, a + nl)
+        s_loc = _windows(s, np.array([a]), nl + M - 1)[0]
+        g_loc = np.zeros((F, nl), np.complex64)
+        for i in cl:
+            f, j0 = support[i]
+            g_loc[f, j0 - a] = vals[i]
+        ds_loc, dh_loc = oracle.adjoint(s_loc, h, g_loc)
+        dh_ref += dh_loc
+        # ds[m] for m in [jmin, jmax + M - 1] sees only this cluster's entries
+        m = np.arange(jmin, min(jmax + M, NS))
+        assert m.max() < NS and a + nl + M - 1 <= NS
+        got.append(ds[torch.from_numpy(m).cuda()].cpu().numpy())
+        want.append(ds_loc[m - a])
+    got, want = np.concatenate(got), np.concatenate(want)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 2e-6
+    far = np.array([1 << 30, (1 << 31) - (1 << 20), 70_000])  # no gradient within 2M of these
+    assert far.max() < NS and all(abs(int(x) - j0) > 2 * M for x in far for _, j0 in support)
+    assert np.all(ds[torch.from_numpy(far).cuda()].cpu().numpy() == 0)
+    assert oracle.max_stream_rel_l2(dh.cpu().numpy(), dh_ref) <= 1e-5
+    plan.close()
+    del ds, s
     torch.cuda.empty_cache()
