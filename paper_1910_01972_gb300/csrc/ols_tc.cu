@@ -14,8 +14,13 @@
 //   shared memory in the no-swizzle K-major core-matrix layout.
 // * D = A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term is below the
 //   16-bit split's resolution), six tcgen05.mma of K = 16 per tile, FP32
-//   accumulation in TMEM; one thread issues them and commits to an mbarrier;
-//   every thread waits (bounded) and reads its row back with tcgen05.ld.
+//   accumulation in TMEM.  Each 128-thread tile synchronises on a named
+//   barrier of its own; its first thread issues the tile's MMAs and commits
+//   them to the tile's mbarrier; the tile's threads wait (bounded) and read
+//   their rows back with tcgen05.ld.
+// * Two filters are in flight (TMEM groups a and b of each tile), skewed by
+//   half a pass: the MMAs of one group run while the other group's threads
+//   read back, exchange, twiddle and split.
 // * Twiddles, the point-wise product and the exchanges between passes stay
 //   in FP32 registers and shared memory, as in the FP32 kernel.  A remainder
 //   pass of radix 2/4/8 (N not a power of 16) stays in FP32 registers.
@@ -23,9 +28,10 @@
 //   before the last forward pass); inverse passes after the first are scaled
 //   by 1/4 (exact), and the filter spectra by 4^(passes-1), which keeps every
 //   16-bit operand below 65504 for inputs with |s| <= 1.42 and unit-L2 filters.
-// Waits on the mbarrier are bounded: on expiry the kernel records an error in
-// the plan's status word, stops, waits (bounded again) for the commit it gave
-// up on, releases its TMEM and returns.  The in-loop limit is a launch
+// Waits on the mbarriers are bounded: on expiry the kernel records an error in
+// the plan's status word and stops at the end of the filter pair; each tile's
+// issuing thread then waits (bounded again) for the commits it issued and did
+// not see complete, and the CTA releases its TMEM and returns.  The in-loop limit is a launch
 // argument (the plan's), and so is a test switch that points the in-loop
 // waits at a second mbarrier nothing ever arrives on, so that a test can make
 // a wait run out without any fault; the drain before the TMEM release always
@@ -43,7 +49,7 @@ namespace ols {
 
 namespace tc {
 
-constexpr int kCols = 64;            // TMEM columns per 128-row tile: A_hi 16, A_lo 16, D 32
+constexpr int kCols = 128;           // TMEM columns per 128-row tile: two groups of A_hi 16, A_lo 16, D 32
 constexpr int kBytesB = 32 * 32 * 2; // one 32x32 16-bit matrix
 constexpr long long kWaitLimit = 1ll << 20;   // polls; also the drain limit before tcgen05.dealloc
 
@@ -106,91 +112,110 @@ __device__ __forceinline__ constexpr uint32_t idesc() {
            ((128u >> 4) << 24);
 }
 
+// Per-thread view of its tile (128 rows = 128 threads = the TMEM lanes of
+// warps 4 tile .. 4 tile + 3).  Two groups of operands per tile, a and b (two
+// filters in flight): group g's A rows (hi: 16 columns, lo: 16) at column
+// 64 g of the tile, its D (32 FP32 columns) at 64 g + 32.  The tile's first
+// thread issues the tile's MMAs and commits them to the group's mbarrier.
 struct Ctx {
-    uint32_t tmem;         // TMEM base of this CTA
-    uint32_t tile_cols;    // column offset of this thread's tile
-    uint32_t lane_bits;    // (warp % 4) * 32 << 16
-    uint32_t mbar;         // shared address of the mbarrier the MMAs commit to
-    uint32_t wbar;         // the one in-loop waits watch: mbar, or (test switch) one nothing arrives on
+    uint32_t lane_base;    // TMEM address of this thread's lane in its tile (column 0 of the tile)
+    uint32_t tile_base;    // TMEM address of the tile (lane 0, column 0) for the MMAs
+    uint32_t mbar[2];      // this tile's mbarriers, groups a and b
+    uint32_t wbar[2];      // what in-loop waits watch: mbar, or (test switch) one nothing arrives on
+    uint32_t phase[2];     // parity expected next; frozen once a wait has run out
     uint32_t b_smem;       // shared address of the four B matrices (fwd hi, fwd lo, inv hi, inv lo)
-    uint32_t phase;        // mbarrier parity expected next; frozen at the pending commit once a wait expired
     long long wait_limit;  // polls per in-loop wait
-    int ntiles;
     int *status;           // plan status word (error flag)
-    bool failed;           // this thread saw a wait expire
-    bool stop;             // some thread of the CTA did (agreed once per filter): leave the loops
+    int tile;
+    bool leader;           // issues this tile's MMAs
+    bool pending[2];       // leader: a commit issued and not yet seen complete
+    bool failed;           // this thread saw a wait run out
+    bool stop;             // some thread of the CTA did (agreed once per filter pair): leave the loops
 };
 
-// One radix-16 DFT pass on the tensor cores for every thread's 16 values,
-// given as the split rows of A: hi[w] / lo[w] pack (Re x_2w, Re x_2w+1) for
-// w < 8 and (Im x_2(w-8), Im x_2(w-8)+1) for w >= 8.  Collective over the CTA.
-template <bool INV, bool BF16>
-__device__ __forceinline__ void dft16_rows(const uint32_t *hi, const uint32_t *lo, float2 *x, Ctx &c) {
-    const uint32_t a_hi = c.tmem + c.lane_bits + c.tile_cols;
-    tmem_st16(a_hi, hi);
-    tmem_st16(a_hi + 16, lo);
+// Group g's A rows from split words: hi[w] / lo[w] pack (Re x_2w, Re x_2w+1)
+// for w < 8 and (Im x_2(w-8), Im x_2(w-8)+1) for w >= 8.
+__device__ __forceinline__ void store_words(const uint32_t *hi, const uint32_t *lo, const Ctx &c, int g) {
+    const uint32_t a = c.lane_base + 64u * (uint32_t)g;
+    tmem_st16(a, hi);
+    tmem_st16(a + 16, lo);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0 && !c.failed) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t bh = c.b_smem + (INV ? 2 : 0) * kBytesB, bl = bh + kBytesB;
-        for (int tl = 0; tl < c.ntiles; ++tl) {
-            const uint32_t base = c.tmem + tl * kCols;
-            const uint32_t d = base + 32;
-#pragma unroll
-            for (int term = 0; term < 3; ++term) {
-                const uint32_t a = base + (term == 2 ? 16 : 0);          // A_hi, A_hi, A_lo
-                const uint32_t b = term == 1 ? bl : bh;                    // B_hi, B_lo, B_hi
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint32_t acc = (term | kk) != 0;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
-                                 "r"(a + kk * 8), "l"(b_desc(b + kk * 1024)), "r"(idesc<BF16>()), "r"(acc)
-                                 : "memory");
-                }
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
-                     : "memory");
-    }
-    uint32_t done = c.failed ? 1u : 0u;
-    for (long long it = 0; it < c.wait_limit && !done; ++it) {
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done)
-                     : "r"(c.wbar), "r"(c.phase)
-                     : "memory");
-    }
-    if (!done) {
-        c.failed = true;
-        atomicOr(c.status, 1);
-    }
-    // no CTA-wide agreement here: every thread goes on along the same path (a
-    // failed thread skips its waits and stores), and the CTA agrees on
-    // stopping once per filter; the barrier before the next MMA issue orders
-    // every thread's read of D before D is overwritten.  A failed thread
-    // keeps c.phase at the parity of the commit it gave up on (the issuing
-    // thread commits nothing after its own failure), which is the one the
-    // drain before the TMEM release must see complete.
-    if (!c.failed) c.phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float d[32];
-    tmem_ld32(c.tmem + c.lane_bits + c.tile_cols + 32, d);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) x[j] = make_float2(d[j], d[16 + j]);
 }
 
-// The same pass on FP32 values (x scaled by `scale` first), split here.
-template <bool INV, bool BF16>
-__device__ __forceinline__ void dft16(float2 *x, float scale, Ctx &c) {
+// Group g's A rows from FP32 values (x scaled by `scale` first), split here.
+template <bool BF16>
+__device__ __forceinline__ void store_rows(const float2 *x, float scale, const Ctx &c, int g) {
     uint32_t hi[16], lo[16];
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
         split2<BF16>(x[2 * w].x * scale, x[2 * w + 1].x * scale, hi[w], lo[w]);
         split2<BF16>(x[2 * w].y * scale, x[2 * w + 1].y * scale, hi[8 + w], lo[8 + w]);
     }
-    dft16_rows<INV, BF16>(hi, lo, x, c);
+    store_words(hi, lo, c, g);
+}
+
+// Every thread of the tile has stored its rows; the leader issues the tile's
+// six MMAs (D = A_hi B_hi + A_hi B_lo + A_lo B_hi, K = 32 as two halves) and
+// commits them to group g's mbarrier.  Collective over the tile.
+template <bool INV, bool BF16>
+__device__ __forceinline__ void issue(Ctx &c, int g) {
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + c.tile) : "memory");
+    if (c.leader && !c.failed) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t bh = c.b_smem + (INV ? 2 : 0) * kBytesB, bl = bh + kBytesB;
+        const uint32_t base = c.tile_base + 64u * (uint32_t)g;
+        const uint32_t d = base + 32;
+#pragma unroll
+        for (int term = 0; term < 3; ++term) {
+            const uint32_t a = base + (term == 2 ? 16 : 0);          // A_hi, A_hi, A_lo
+            const uint32_t b = term == 1 ? bl : bh;                    // B_hi, B_lo, B_hi
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint32_t acc = (term | kk) != 0;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+                             "r"(a + kk * 8), "l"(b_desc(b + kk * 1024)), "r"(idesc<BF16>()), "r"(acc)
+                             : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar[g])
+                     : "memory");
+        c.pending[g] = true;
+    }
+}
+
+// Bounded poll of mbarrier `bar` for parity `phase`; true once it completed.
+__device__ __forceinline__ bool poll(uint32_t bar, uint32_t phase, long long limit) {
+    uint32_t done = 0;
+    for (long long it = 0; it < limit && !done; ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(phase)
+                     : "memory");
+    }
+    return done != 0;
+}
+
+// Wait (bounded) for group g's MMAs and read this thread's row of D into x.
+// A thread whose wait runs out records it, keeps the group's parity (so the
+// leader's drain before the TMEM release watches the commit it gave up on)
+// and skips its later waits; its results are then undefined and not stored.
+__device__ __forceinline__ void wait_load(float2 *x, Ctx &c, int g) {
+    if (!c.failed) {
+        if (poll(c.wbar[g], c.phase[g], c.wait_limit)) {
+            c.phase[g] ^= 1u;
+            c.pending[g] = false;
+        } else {
+            c.failed = true;
+            atomicOr(c.status, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float d[32];
+    tmem_ld32(c.lane_base + 64u * (uint32_t)g + 32, d);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = make_float2(d[j], d[16 + j]);
 }
 
 // Rows of A from samples already stored split: hs[k] / ls[k] hold
@@ -205,17 +230,19 @@ __device__ __forceinline__ void rows_from_planes(const uint32_t *hs, const uint3
     }
 }
 
-// Forward passes P.. on x.  With PRE (pre-split input) the first pass takes
-// its A rows as given (rows_hi / rows_lo) instead of splitting x.
+// Forward passes P.. of the segment (once per segment, group a, no overlap).
+// With PRE (pre-split input) the first pass takes its A rows as given
+// (rows_hi / rows_lo) instead of splitting x.
 template <int LOG2N, int P, bool BF16, bool PRE = false>
 __device__ __forceinline__ void tc_forward_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc, Ctx &c,
                                                   const uint32_t *rows_hi = nullptr, const uint32_t *rows_lo = nullptr) {
     using G = Geo<LOG2N>;
     static_assert(G::radix(0) == 16, "the first forward pass is radix 16 for every supported N");
-    if constexpr (P == 0 && PRE) {
-        dft16_rows<false, BF16>(rows_hi, rows_lo, x, c);
-    } else if constexpr (G::radix(P) == 16) {
-        dft16<false, BF16>(x, 1.0f, c);
+    if constexpr (G::radix(P) == 16) {
+        if constexpr (P == 0 && PRE) store_words(rows_hi, rows_lo, c, 0);
+        else store_rows<BF16>(x, 1.0f, c, 0);
+        issue<false, BF16>(c, 0);
+        wait_load(x, c, 0);
     } else {
         dft_groups<G::radix(P), false>(x);
     }
@@ -227,18 +254,51 @@ __device__ __forceinline__ void tc_forward_passes(float2 *x, float2 *bufs, const
     }
 }
 
+// Inverse passes P, P-1, ..., 0 of two filters in flight (group a: xa, group
+// b: xb), skewed by half a pass: the MMAs of a's pass P run while b finishes
+// pass P+1 and prepares pass P (wait, exchange, twiddle, split), and those of
+// b's pass P while a finishes pass P and prepares pass P-1.  Inverse passes
+// after the first are scaled by 1/4 (exact; the spectra carry the gain).
 template <int LOG2N, int P, bool BF16>
-__device__ __forceinline__ void tc_inverse_passes(float2 *x, float2 *bufs, const float2 *tw, int t, int &xc,
-                                                  Ctx &c) {
+__device__ __forceinline__ void tc_inverse_pair(float2 *xa, float2 *xb, float2 *bufs, const float2 *tw, int t,
+                                                int &xc, Ctx &c) {
     using G = Geo<LOG2N>;
+    constexpr bool TCP = G::radix(P) == 16;                                  // pass P on the tensor cores
+    constexpr bool B_IN_FLIGHT = P + 1 <= G::NP - 1 && G::radix(P + 1) == 16; // b's pass P+1 not read back yet
+    constexpr float scale = P == G::NP - 1 ? 1.0f : 0.25f;
+    // a: enter pass P
     if constexpr (P < G::NP - 1) {
-        exchange<LOG2N, P + 1, P>(x, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
+        exchange<LOG2N, P + 1, P>(xa, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
         ++xc;
-        twiddle<LOG2N, P, true>(x, tw, t);
+        twiddle<LOG2N, P, true>(xa, tw, t);
     }
-    if constexpr (G::radix(P) == 16) dft16<true, BF16>(x, P == G::NP - 1 ? 1.0f : 0.25f, c);
-    else dft_groups<G::radix(P), true>(x);
-    if constexpr (P > 0) tc_inverse_passes<LOG2N, P - 1, BF16>(x, bufs, tw, t, xc, c);
+    if constexpr (TCP) {
+        store_rows<BF16>(xa, scale, c, 0);
+        issue<true, BF16>(c, 0);
+    } else {
+        dft_groups<G::radix(P), true>(xa);
+    }
+    // b: finish pass P+1, enter pass P
+    if constexpr (B_IN_FLIGHT) wait_load(xb, c, 1);
+    if constexpr (P < G::NP - 1) {
+        exchange<LOG2N, P + 1, P>(xb, bufs + (G::XBUFS == 2 ? (xc & 1) * G::PADN : 0), t);
+        ++xc;
+        twiddle<LOG2N, P, true>(xb, tw, t);
+    }
+    if constexpr (TCP) {
+        store_rows<BF16>(xb, scale, c, 1);
+        issue<true, BF16>(c, 1);
+    } else {
+        dft_groups<G::radix(P), true>(xb);
+    }
+    // a: finish pass P
+    if constexpr (TCP) wait_load(xa, c, 0);
+    if constexpr (P > 0) {
+        tc_inverse_pair<LOG2N, P - 1, BF16>(xa, xb, bufs, tw, t, xc, c);
+    } else {
+        static_assert(TCP, "pass 0 is radix 16");
+        wait_load(xb, c, 1);                         // b: finish pass 0
+    }
 }
 
 // Inverse passes after the first are scaled by 1/4: the spectra get 4^(k),
@@ -267,7 +327,7 @@ ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_h
     constexpr uint32_t NCOLS = NT * tc::kCols;
     static_assert(G::BLOCK % 128 == 0, "the tensor-core form needs 128-thread multiples");
     extern __shared__ float4 smem_raw[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[NT][2];   // per tile, groups a and b
     __shared__ __align__(8) uint64_t mbar_never;   // test switch: no thread or MMA ever arrives here
     __shared__ uint32_t tbase;
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
@@ -280,7 +340,9 @@ ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_h
 
     for (int i = threadIdx.x; i < 4 * tc::kBytesB / 2; i += G::BLOCK) bsm[i] = bmat[i];
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+        for (int i = 0; i < NT; ++i)
+            for (int g = 0; g < 2; ++g)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar[i][g])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar_never)));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -294,16 +356,19 @@ ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_h
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     tc::Ctx c;
-    c.tmem = tbase;
-    c.tile_cols = (uint32_t)(threadIdx.x / 128) * tc::kCols;
-    c.lane_bits = (uint32_t)(((threadIdx.x / 32) % 4) * 32) << 16;
-    c.mbar = tc::smem_u32(&mbar);
-    c.wbar = wait_never ? tc::smem_u32(&mbar_never) : c.mbar;
+    c.tile = threadIdx.x / 128;
+    c.tile_base = tbase + (uint32_t)c.tile * tc::kCols;
+    c.lane_base = c.tile_base + ((uint32_t)(((threadIdx.x / 32) % 4) * 32) << 16);
+    for (int g = 0; g < 2; ++g) {
+        c.mbar[g] = tc::smem_u32(&mbar[c.tile][g]);
+        c.wbar[g] = wait_never ? tc::smem_u32(&mbar_never) : c.mbar[g];
+        c.phase[g] = 0;
+        c.pending[g] = false;
+    }
     c.b_smem = tc::smem_u32(bsm);
-    c.phase = 0;
     c.wait_limit = wait_limit;
-    c.ntiles = NT;
     c.status = status;
+    c.leader = threadIdx.x % 128 == 0;
     c.failed = false;
     c.stop = false;
 
@@ -341,36 +406,45 @@ ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_h
         const long long rem = active ? (Nout - start) : 0;
         const int span = (int)(rem < (long long)(G::N - lo) ? rem : (long long)(G::N - lo));
         const long long obase = start - lo;
-        for (int f = 0; f < F && !c.stop; ++f) {
-            float2 x[16];
-            const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
+        // filters in pairs (two in flight); an odd bank's last filter runs as
+        // both groups and only group a's result is stored
+        for (int f = 0; f < F && !c.stop; f += 2) {
+            const int fb = f + 1 < F ? f + 1 : f;
+            float2 xa[16], xb[16];
+            const float4 *ha = Hk + (size_t)f * (G::N / 2) + t, *hb = Hk + (size_t)fb * (G::N / 2) + t;
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2) {
-                const float4 h = load_spectrum(hp + j2 * G::T);
-                x[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
-                x[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
+                const float4 h = load_spectrum(ha + j2 * G::T);
+                xa[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
+                xa[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
             }
-            tc::tc_inverse_passes<LOG2N, G::NP - 1, BF16>(x, bufs, tw, t, xc, c);
-            float2 *dst = y + (size_t)f * (size_t)Nout;
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) {
+                const float4 h = load_spectrum(hb + j2 * G::T);
+                xb[2 * j2] = cmul(X[2 * j2], make_float2(h.x, h.y));
+                xb[2 * j2 + 1] = cmul(X[2 * j2 + 1], make_float2(h.z, h.w));
+            }
+            tc::tc_inverse_pair<LOG2N, G::NP - 1, BF16>(xa, xb, bufs, tw, t, xc, c);
             if (!c.failed) {
+                float2 *da = y + (size_t)f * (size_t)Nout, *db = y + (size_t)fb * (size_t)Nout;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int n = k * G::T + t;
-                    if ((unsigned)(n - lo) < (unsigned)span) dst[obase + n] = x[k];
+                    if ((unsigned)(n - lo) < (unsigned)span) {
+                        da[obase + n] = xa[k];
+                        if (fb != f) db[obase + n] = xb[k];
+                    }
                 }
             }
-            c.stop = __syncthreads_or(c.failed) != 0;   // the CTA's agreement, once per filter
+            c.stop = __syncthreads_or(c.failed) != 0;   // the CTA's agreement, once per filter pair
         }
     }
-    // release TMEM (after a bounded wait for the commit a failed thread gave up on)
-    if (c.failed) {
-        uint32_t done = 0;
-        for (long long it = 0; it < tc::kWaitLimit && !done; ++it) {
-            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                         : "=r"(done)
-                         : "r"(c.mbar), "r"(c.phase)
-                         : "memory");
-        }
+    // release TMEM: a tile's leader first waits (bounded, long limit) for every
+    // commit it issued and did not see complete -- after a wait ran out, at most
+    // one per group, at the parity the group's phase kept
+    if (c.leader) {
+        for (int g = 0; g < 2; ++g)
+            if (c.pending[g]) tc::poll(c.mbar[g], c.phase[g], tc::kWaitLimit);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
