@@ -1,9 +1,10 @@
 """The filter-bank split across ranks (parallel.FilterSplit) with the
 library's kernels on every rank.
 
-World size 2 over gloo (host collectives), both ranks on cuda:0: the ranks'
-kernels are independent launches that never wait on one another, and the
-only exchanges (row gather, ds sum) go through host memory.  Rank 0 checks
+World size 2 and 3 over gloo (host collectives), every rank on cuda:0: the
+ranks' kernels are independent launches that never wait on one another, and
+the only exchanges (row gather, ds sum) go through host memory.  Blocks of
+uneven size and idle ranks (F < world size) included.  Rank 0 checks
 y, ds and dh against the FP64 oracle at the parity tolerances, and y and dh
 bit for bit against one unsplit plan (each filter's rows come from the same
 kernel arithmetic whichever plan holds the filter)."""
@@ -74,9 +75,9 @@ def _worker(rank, world, port, Ns, M, F, N, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("F", [5, 1])
-def test_filter_split_two_ranks_runs_the_kernels(F):
-    world, Ns, M, N = 2, 50_000, 129, 1024
+@pytest.mark.parametrize("F,world", [(5, 2), (1, 2), (7, 3), (2, 3)])
+def test_filter_split_ranks_run_the_kernels(F, world):
+    Ns, M, N = 50_000, 129, 1024
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()

@@ -152,7 +152,11 @@ def test_split_signal_rounding(flag):
 
 @pytest.mark.parametrize("flag", FLAGS)
 @pytest.mark.parametrize("N,M,F,Ns", [(4096, 512, 3, 100_000), (256, 33, 2, 20_001), (2048, 257, 2, 9_001),
-                                      (8192, 1025, 1, 40_000), (512, 1, 2, 700)])
+                                      (8192, 1025, 1, 40_000), (512, 1, 2, 700),
+                                      (1024, 129, 3, 129),          # Ns = M: one output
+                                      (1024, 100, 2, 900),          # Ns < N: one segment, zero-filled
+                                      (512, 257, 5, 7_000),         # M - 1 = L: overlaps meet exactly
+                                      (4096, 4096, 1, 9_000)])      # M = N: one output per segment
 def test_convolve_split_equals_convolve(flag, N, M, F, Ns):
     """Planes from split_signal give bit for bit the FP32-input result: the
     first forward stage gets the same operands either way."""
