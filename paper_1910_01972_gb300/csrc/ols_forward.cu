@@ -26,8 +26,9 @@
 // * Global loads and stores: for each register k, consecutive threads touch
 //   consecutive samples (fully coalesced); the valid-output test is one
 //   unsigned compare per sample.
-// * Persistent grid sized from the SM's registers, shared memory, threads and
-//   TMEM columns: resident blocks loop over segments.
+// * Residency computed from the SM's registers, shared memory, threads and
+//   TMEM columns; blocks loop over segments (persistent grid from N = 4096,
+//   one block per segment block below: see fused_grid).
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -119,7 +120,7 @@ static cudaError_t launch_one(const ols_plan_s &p, const float2 *s, int64_t Ns, 
                               int64_t nseg, int64_t Nout, cudaStream_t st) {
     using G = Geo<LOG2N>;
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
-    const int grid = (int)(nblk < p.fwd_grid_cap ? nblk : p.fwd_grid_cap);
+    const int grid = fused_grid(LOG2N, nblk, p.fwd_grid_cap);
     ols_forward_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM_TMEM, st>>>(
         s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y, p.M, p.F, L, nseg, Nout);
     return cudaGetLastError();

@@ -49,6 +49,20 @@ struct AllocScope {      // nests: only the outermost scope restarts the count
     ~AllocScope();
 };
 
+// Grid of the fused forward and real-to-real kernels.  Up to N = 2048: one
+// CTA per block of segments, left to the hardware scheduler, which starts a
+// CTA wherever one finishes and so balances the last wave (the persistent
+// grid gives every CTA a fixed share of segments: measured 1% slower on the
+// 2^23-sample bank at N = 2048, 4% at N = 1024, 0.9% for the real form).
+// From N = 4096 the persistent grid, whose CTAs set up their twiddles and
+// tensor memory once (0.7% faster there).  Either way the shared memory each
+// CTA requests bounds residency to what tensor memory can serve.
+inline int fused_grid(int log2N, int64_t nblk, int persistent_cap) {
+    int64_t g = (log2N <= 11) ? nblk : (nblk < persistent_cap ? nblk : persistent_cap);
+    if (g > 0x7fffffff) g = 0x7fffffff;   // grid.x limit; the kernels loop over the rest
+    return (int)g;
+}
+
 struct Staging {            // device buffers of ols_convolve_host
     float2 *in[2] = {nullptr, nullptr};
     float2 *out[2] = {nullptr, nullptr};

@@ -179,7 +179,7 @@ static cudaError_t r2r_launch_n(const ols_plan_s &p, const float *s, int64_t Ns,
                                 int64_t Nout, cudaStream_t st) {
     using G = Geo<LOG2N>;
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
-    const int grid = (int)(nblk < p.r2r_grid_cap ? nblk : p.r2r_grid_cap);
+    const int grid = fused_grid(LOG2N, nblk, p.r2r_grid_cap);
     ols_r2r_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM_TMEM, st>>>(s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y,
                                                            p.M, p.F, L, nseg, Nout);
     return cudaGetLastError();
