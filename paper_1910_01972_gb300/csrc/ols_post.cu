@@ -30,7 +30,13 @@ template <int LOG2N, int MODE>
 struct PostGeo {
     using G = Geo<LOG2N>;
     static constexpr int BUFS = G::XBUFS + (MODE == POST_DERIV ? 1 : 0);
-    static constexpr size_t SMEM = sizeof(float2) * (size_t)(G::SEGS * BUFS * G::PADN);
+    static constexpr size_t SMEM_USED = sizeof(float2) * (size_t)(G::SEGS * BUFS * G::PADN);
+    // requested: at least enough that no more blocks fit on an SM (228 KB)
+    // than TMEM can serve, so a block's tcgen05.alloc never waits
+    static constexpr size_t SMEM = !OLS_FWD_TW_TMEM ? SMEM_USED
+                                   : (SMEM_USED > (228u * 1024u) / (G::TMEM_MAX_CTAS + 1))
+                                       ? SMEM_USED
+                                       : (228u * 1024u) / (G::TMEM_MAX_CTAS + 1) + 1024u;
     // the derivative's epilogue holds more live values: one resident block
     // fewer per SM keeps it free of register spills
     static constexpr int MINB = (MODE == POST_DERIV && G::MINB > 1) ? G::MINB - 1 : G::MINB;
@@ -236,7 +242,7 @@ static cudaError_t post_launch_nm(const ols_plan_s &p, const PostArgs &a, cudaSt
     using PG = PostGeo<LOG2N, MODE>;
     const int64_t nblk = (a.nseg + G::SEGS - 1) / G::SEGS;
     const int cap = p.post_grid_cap[MODE];
-    const int grid = (int)(nblk < cap ? nblk : cap);
+    const int grid = fused_grid(LOG2N, nblk, cap);
     ols_post_kernel<LOG2N, MODE><<<grid, G::BLOCK, PG::SMEM, st>>>(
         a.s, a.Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, a.out, p.M, p.F, a.step, a.nseg, a.Nout, a.thr,
         a.cand, a.count, a.cap);
