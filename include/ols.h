@@ -431,10 +431,14 @@ OLS_API int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const vo
 OLS_API int ols_batch_last_launch_count(ols_batch_t batch);
 
 /*
- * Read the plan's device status word (synchronises the device): 0, or
- * nonzero if a kernel's bounded wait on the tensor cores gave up since the
- * last reset (that call's output is incomplete).  reset != 0 clears it.
- * Errors: INVALID, CUDA.
+ * Read the plan's device status word (synchronises the device): 0, or the
+ * OR of these bits since the last reset (that call's output is then
+ * incomplete):
+ *   1  a kernel's bounded wait on the tensor cores gave up;
+ *   2  (only in a library built with OLS_CHECK=1, a debug build) a global
+ *      memory access of the forward, tensor-core or adjoint kernels failed
+ *      its bounds check against its buffer and was skipped.
+ * reset != 0 clears it.  Errors: INVALID, CUDA.
  */
 OLS_API int ols_plan_status(ols_plan_t plan, int *status, int reset);
 

@@ -12,7 +12,9 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libols.so")
+# OLS_LIBRARY selects another build of the library (e.g. the bounds-checked
+# debug build, libols_check.so); default: the in-tree libols.so.
+LIB_PATH = os.environ.get("OLS_LIBRARY") or os.path.join(_HERE, "libols.so")
 
 OLS_OK = 0
 OLS_ERR_INVALID = 1

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(BwdGeo<LOG2N>::BLOCK, BwdGeo<LOG2N>::MINB)
 ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *__restrict__ g,
                     long long Nout, const float4 *__restrict__ Htk, const float2 *__restrict__ twg,
                     float2 *__restrict__ ds, float2 *__restrict__ edge, float4 *__restrict__ P,
-                    int M, int F, long long L, long long nseg) {
+                    int M, int F, long long L, long long nseg, int *status) {
     using G = Geo<LOG2N>;
     using BG = BwdGeo<LOG2N>;
     extern __shared__ float4 smem_raw[];
@@ -191,7 +191,9 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             const int lim = (int)(avail < G::N ? avail : G::N);
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                A[k] = (k * G::T + t < lim) ? ld_stream(sig + start + k * G::T + t, l2) : make_float2(0.f, 0.f);
+                A[k] = (k * G::T + t < lim && in_bounds(start + k * G::T + t < Ns, status))
+                           ? ld_stream(sig + start + k * G::T + t, l2)
+                           : make_float2(0.f, 0.f);
             forward_passes<LOG2N, 0>(A, bufs, tw, t, xc, bar);
 #if OLS_BWD_TW_TMEM
             tmem::st32(acol, reinterpret_cast<const float *>(A));
@@ -216,7 +218,10 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
             float2 b[16];
             const float2 *gf = g + (size_t)f * (size_t)Nout + start + t;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) b[k] = (k * G::T + t < gl) ? ld_stream(gf + k * G::T, l2) : make_float2(0.f, 0.f);
+            for (int k = 0; k < 16; ++k)
+                b[k] = (k * G::T + t < gl && in_bounds(start + k * G::T + t < Nout, status))
+                           ? ld_stream(gf + k * G::T, l2)
+                           : make_float2(0.f, 0.f);
 #if OLS_BWD_PREFETCH
             // a window is at most N/16 = T lines of 128 B: one line per thread
             if (f + 1 < F) {
@@ -232,7 +237,10 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
                 const float4 *hp = Htk + (size_t)f * BG::HALF + t;
 #pragma unroll
                 for (int j2 = 0; j2 < 8; ++j2) {
-                    const float4 h = load_spectrum(hp + j2 * G::T);
+                    const float4 h = in_bounds((long long)f * BG::HALF + j2 * G::T + t < (long long)F * BG::HALF,
+                                               status)
+                                         ? load_spectrum(hp + j2 * G::T)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
                     D[2 * j2] = cadd(D[2 * j2], cmul(b[2 * j2], make_float2(h.x, h.y)));
                     D[2 * j2 + 1] = cadd(D[2 * j2 + 1], cmul(b[2 * j2 + 1], make_float2(h.z, h.w)));
                 }
@@ -268,6 +276,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
 #pragma unroll
                     for (int j2 = 0; j2 < 8; ++j2) {
                         float4 *dst = Pf + j2 * G::T + t;
+                        if (!in_bounds(j2 * G::T + t < BG::HALF, status)) continue;
                         if (first) st_keep(dst, q[j2], l2);
                         else red_add(dst, q[j2], l2);
                     }
@@ -285,6 +294,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
                         float4 acc = prod[e];
 #pragma unroll
                         for (int s2 = 1; s2 < BG::SLOTS; ++s2) acc = f4add(acc, prod[s2 * SSTRIDE + e]);
+                        if (!in_bounds(e < BG::HALF, status)) continue;
                         if (first) st_keep(Pf + e, acc, l2);
                         else red_add(Pf + e, acc, l2);
                     }
@@ -302,7 +312,7 @@ ols_backward_kernel(const float2 *__restrict__ sig, long long Ns, const float2 *
                     if (u < lo) {
                         eh[u] = D[k];
                     } else if (u >= Li) {
-                        eh[lo + (u - Li)] = D[k];
+                        if (in_bounds(u - Li < lo, status)) eh[lo + (u - Li)] = D[k];
                     } else if (start + u < Ns) {
                         ds[start + u] = D[k];
                     }
@@ -333,7 +343,7 @@ constexpr int kFinishLanes = 8;   // threads per dh spectrum entry in the finish
 __global__ void __launch_bounds__(256)
 ols_backward_finish_kernel(const float2 *__restrict__ edge, float2 *__restrict__ ds, long long Ns, long long L,
                            long long nseg, int M, const float4 *__restrict__ P, int npart,
-                           float4 *__restrict__ Pr, long long FH) {
+                           float4 *__restrict__ Pr, long long FH, int *status) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nred = Pr ? FH * kFinishLanes : 0;
     if (gid < nred) {
@@ -371,7 +381,7 @@ ols_backward_finish_kernel(const float2 *__restrict__ edge, float2 *__restrict__
     const long long b = e / lo;
     const int u = (int)(e % lo);
     const long long m = b * L + u;
-    if (m >= Ns) return;
+    if (m >= Ns || !in_bounds(m >= 0 && b <= nseg, status)) return;
     float2 v = make_float2(0.f, 0.f);
     if (b < nseg) v = edge[(size_t)b * 2 * lo + u];
     if (b > 0) {
@@ -482,7 +492,7 @@ static void launch_bwd_one(const ols_plan_s &p, const BackwardArgs &a, cudaStrea
     using BG = BwdGeo<LOG2N>;
     ols_backward_kernel<LOG2N, DS, DH><<<a.grid, BG::BLOCK, BG::SMEM, st>>>(
         a.s, a.Ns, a.g, a.Nout, reinterpret_cast<const float4 *>(p.Htk), p.tw, a.ds, a.edge, a.P, p.M, p.F, a.L,
-        a.nseg);
+        a.nseg, p.d_status);
 }
 
 template <int LOG2N>
@@ -518,7 +528,7 @@ cudaError_t launch_backward(const ols_plan_s &p, const BackwardArgs &a, cudaStre
     const long long total = FH * kFinishLanes + nfix;
     if (total > 0) {
         ols_backward_finish_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-            a.edge, a.ds, a.Ns, a.L, a.nseg, p.M, a.P, a.grid, a.dh ? a.Pr : nullptr, FH);
+            a.edge, a.ds, a.Ns, a.L, a.nseg, p.M, a.P, a.grid, a.dh ? a.Pr : nullptr, FH, p.d_status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         *launches = 2;

@@ -59,8 +59,30 @@
 #ifndef OLS_WARPS_PER_SM
 #define OLS_WARPS_PER_SM 16  // resident warps per SM the register budget must allow
 #endif
+#ifndef OLS_CHECK
+#define OLS_CHECK 0          // 1: debug build, every global access of the main kernels bounds-checked
+#endif
 
 namespace ols {
+
+// Bits of a plan's device status word.
+constexpr int kStatusWaitExpired = 1;   // a bounded device wait gave up
+constexpr int kStatusOutOfBounds = 2;   // (OLS_CHECK builds) an index failed its bounds check
+
+// In a build with OLS_CHECK=1: `ok`, and a false check is recorded in the
+// status word (the caller then skips the access) -- a bounds checker that
+// needs no external tool and never traps.  In a normal build: true, and the
+// check compiles away.
+__device__ __forceinline__ bool in_bounds(bool ok, int *status) {
+#if OLS_CHECK
+    if (!ok && status) atomicOr(status, kStatusOutOfBounds);
+    return ok;
+#else
+    (void)ok;
+    (void)status;
+    return true;
+#endif
+}
 
 template <int LOG2N>
 struct Geo {

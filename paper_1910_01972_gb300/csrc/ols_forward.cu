@@ -41,7 +41,7 @@ template <int LOG2N>
 __global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, Geo<LOG2N>::MINB)
 ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
                    const float2 *__restrict__ twg, float2 *__restrict__ y, int M, int F,
-                   long long L, long long nseg, long long Nout) {
+                   long long L, long long nseg, long long Nout, int *status) {
     using G = Geo<LOG2N>;
     extern __shared__ float4 smem_raw[];
     __shared__ uint32_t tbase;
@@ -76,10 +76,10 @@ ols_forward_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *_
     for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
         const long long seg = blk * G::SEGS + slot;
 #if OLS_FWD_TW_TMEM
-        ols_segment<LOG2N>(sig, Ns, Hk, tw, y, M, F, L, Nout, seg, seg < nseg, bufs, t, xc);
+        ols_segment<LOG2N>(sig, Ns, Hk, tw, y, M, F, L, Nout, seg, seg < nseg, bufs, t, xc, 0u, CtaBarrier{}, status);
 #else
         ols_segment<LOG2N, TwGlobal, OLS_FWD_X_TMEM != 0>(sig, Ns, Hk, tw, y, M, F, L, Nout, seg, seg < nseg, bufs,
-                                                          t, xc, xcol_t);
+                                                          t, xc, xcol_t, CtaBarrier{}, status);
 #endif
     }
 #if OLS_FWD_X_TMEM && !OLS_FWD_TW_TMEM
@@ -122,7 +122,7 @@ static cudaError_t launch_one(const ols_plan_s &p, const float2 *s, int64_t Ns, 
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
     const int grid = fused_grid(LOG2N, nblk, p.fwd_grid_cap);
     ols_forward_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM_TMEM, st>>>(
-        s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y, p.M, p.F, L, nseg, Nout);
+        s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y, p.M, p.F, L, nseg, Nout, p.d_status);
     return cudaGetLastError();
 }
 

@@ -16,13 +16,15 @@ namespace ols {
 // XT: the segment spectrum waits in the thread's TMEM lane at column xcol_t
 // (32 columns) instead of registers; implied by TMEM twiddles (columns 96..127).
 // BAR: the barrier of the segment's exchanges (the whole CTA by default, or
-// only the segment's own threads).
+// only the segment's own threads).  status: the plan's status word, for the
+// bounds checks of OLS_CHECK builds (may be null).
 template <int LOG2N, class TW, bool XT = is_tw_tmem<TW>::value, class BAR = CtaBarrier>
 __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long long Ns,
                                             const float4 *__restrict__ Hk, const TW &tw,
                                             float2 *__restrict__ y, int M, int F, long long L,
                                             long long Nout, long long seg, bool active, float2 *bufs,
-                                            int t, int &xc, uint32_t xcol_t = 0, const BAR &bar = BAR{}) {
+                                            int t, int &xc, uint32_t xcol_t = 0, const BAR &bar = BAR{},
+                                            int *status = nullptr) {
     using G = Geo<LOG2N>;
     const int lo = M - 1;                      // aliased samples per segment
     const long long start = seg * L;
@@ -35,7 +37,9 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
         const float2 *src = sig + (active ? start : 0) + t;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+            X[k] = (k * G::T + t < lim && in_bounds((active ? start : 0) + k * G::T + t < Ns, status))
+                       ? __ldg(src + k * G::T)
+                       : make_float2(0.f, 0.f);
     }
     forward_passes<LOG2N, 0>(X, bufs, tw, t, xc, bar);
     constexpr bool x_in_tmem = XT;
@@ -58,9 +62,11 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
     // against 0.166 ms at Ns = 2^22, N = 4096 0.664 against 0.714 ms)
     constexpr bool prefetch = OLS_PREFETCH_H && !(G::TX_NOPF && tw_xchg<TW>());
     float4 hn[8];
+    const long long hn_end = (long long)F * (G::N / 2);   // float4 entries of the spectra
     if constexpr (prefetch) {
 #pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
+        for (int j2 = 0; j2 < 8; ++j2)
+            if (in_bounds(j2 * G::T + t < hn_end, status)) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
     }
     for (int f = 0; f < F; ++f) {
         float2 x[16];
@@ -74,7 +80,9 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
         if constexpr (!prefetch) {
             const float4 *hp = Hk + (size_t)f * (G::N / 2) + t;
 #pragma unroll
-            for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+            for (int j2 = 0; j2 < 8; ++j2)
+                if (in_bounds((long long)f * (G::N / 2) + j2 * G::T + t < hn_end, status))
+                    hn[j2] = load_spectrum(hp + j2 * G::T);
         }
 #pragma unroll
         for (int j2 = 0; j2 < 8; ++j2) {
@@ -85,7 +93,9 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
             if (f + 1 < F) {
                 const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
 #pragma unroll
-                for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+                for (int j2 = 0; j2 < 8; ++j2)
+                    if (in_bounds((long long)(f + 1) * (G::N / 2) + j2 * G::T + t < hn_end, status))
+                        hn[j2] = load_spectrum(hp + j2 * G::T);
             }
         }
         inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc, bar);
@@ -93,7 +103,8 @@ __device__ __forceinline__ void ols_segment(const float2 *__restrict__ sig, long
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int n = k * G::T + t;
-            if ((unsigned)(n - lo) < (unsigned)span) dst[obase + n] = x[k];
+            if ((unsigned)(n - lo) < (unsigned)span && in_bounds(obase + n >= 0 && obase + n < Nout, status))
+                dst[obase + n] = x[k];
         }
     }
 }

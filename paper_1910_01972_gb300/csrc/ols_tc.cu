@@ -388,7 +388,7 @@ ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_h
             const uint32_t *sh = sig_hi + (active ? start : 0) + t, *sl = sig_lo + (active ? start : 0) + t;
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                const bool in = k * G::T + t < lim;
+                const bool in = k * G::T + t < lim && in_bounds((active ? start : 0) + k * G::T + t < Ns, status);
                 hs[k] = in ? __ldg(sh + k * G::T) : 0u;
                 ls[k] = in ? __ldg(sl + k * G::T) : 0u;
             }
@@ -398,7 +398,9 @@ ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_h
             const float2 *src = sig + (active ? start : 0) + t;
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                X[k] = (k * G::T + t < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+                X[k] = (k * G::T + t < lim && in_bounds((active ? start : 0) + k * G::T + t < Ns, status))
+                           ? __ldg(src + k * G::T)
+                           : make_float2(0.f, 0.f);
             tc::tc_forward_passes<LOG2N, 0, BF16>(X, bufs, tw, t, xc, c);
         }
 #pragma unroll
@@ -430,7 +432,7 @@ ols_tc_kernel(const float2 *__restrict__ sig, const uint32_t *__restrict__ sig_h
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int n = k * G::T + t;
-                    if ((unsigned)(n - lo) < (unsigned)span) {
+                    if ((unsigned)(n - lo) < (unsigned)span && in_bounds(obase + n >= 0 && obase + n < Nout, status)) {
                         da[obase + n] = xa[k];
                         if (fb != f) db[obase + n] = xb[k];
                     }
