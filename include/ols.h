@@ -436,11 +436,17 @@ OLS_API int ols_batch_last_launch_count(ols_batch_t batch);
  * incomplete):
  *   1  a kernel's bounded wait on the tensor cores gave up;
  *   2  (only in a library built with OLS_CHECK=1, a debug build) a global
- *      memory access of the forward, tensor-core or adjoint kernels failed
- *      its bounds check against its buffer and was skipped.
+ *      memory access of a kernel (forward, real-to-real, post-processing,
+ *      tensor-core, adjoint, batched) failed its bounds check against its
+ *      buffer and was skipped.
  * reset != 0 clears it.  Errors: INVALID, CUDA.
  */
 OLS_API int ols_plan_status(ols_plan_t plan, int *status, int reset);
+
+/* The OR of ols_plan_status over every problem of a batch (the batched
+ * kernels report into each problem's own plan status word); reset != 0
+ * clears them all.  Errors: INVALID, CUDA. */
+OLS_API int ols_batch_status(ols_batch_t batch, int *status, int reset);
 
 /* Size in bytes of the scratch array built into the library for
  * ols_convolve_backward_noalloc. */

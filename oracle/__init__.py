@@ -282,10 +282,36 @@ def rel_l2(y, y_ref) -> float:
     return float(num / den) if den > 0 else float(num)
 
 
-def max_stream_rel_l2(y, y_ref) -> float:
-    """Largest per-stream relative L2 error over the leading (filter) axis."""
+def max_stream_rel_l2(y, y_ref, floor=None) -> float:
+    """Largest per-stream relative L2 error over the leading (filter) axis.
+    floor (one value per stream, e.g. ``stream_scale``): the denominator is
+    max(||y_ref_f||, floor_f)."""
     y = np.asarray(y)
     y_ref = np.asarray(y_ref)
     if y.ndim == 1:
-        return rel_l2(y, y_ref)
-    return max(rel_l2(y[f], y_ref[f]) for f in range(y.shape[0]))
+        y, y_ref = y[None], y_ref[None]
+    out = 0.0
+    for f in range(y.shape[0]):
+        num = np.linalg.norm((y[f].astype(np.complex128) - y_ref[f]).ravel())
+        den = np.linalg.norm(np.asarray(y_ref[f], dtype=np.complex128).ravel())
+        if floor is not None:
+            den = max(den, float(np.ravel(floor)[f]))
+        out = max(out, float(num / den) if den > 0 else float(num))
+    return out
+
+
+def stream_scale(s, h, Nout) -> np.ndarray:
+    """Expected norm of each output stream for a white signal:
+    sqrt(Nout) ||h_f||_2 rms(s), since E|y_f[j]|^2 = ||h_f||^2 E|s|^2 by
+    Eq. 1.  A stream of a few outputs can have a norm far below it by chance
+    (one output of a random signal can be near zero), while the rounding
+    error of an FFT-based convolution scales with the segment's and the
+    filter's energy, not with that output; this is the floor of the
+    denominator that makes the relative error of such streams meaningful.
+    For long streams ||y_f|| is close to it and the floor has no effect."""
+    s = np.asarray(s)
+    h = np.asarray(h)
+    if h.ndim == 1:
+        h = h[None]
+    rms = np.linalg.norm(s.astype(np.complex128)) / np.sqrt(max(s.size, 1))
+    return np.sqrt(Nout) * np.linalg.norm(h.astype(np.complex128), axis=1) * rms

@@ -10,6 +10,7 @@ in the library's kernels.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import _native
@@ -305,7 +306,8 @@ class Plan:
         return _native.ols_last_launch_count(self._h)
 
     def status(self, reset: bool = True) -> int:
-        """Device status word: nonzero if a bounded tensor-core wait gave up."""
+        """Device status word: bit 1 a bounded tensor-core wait gave up, bit 2
+        (OLS_CHECK builds) a global access failed its bounds check."""
         rc, v = _native.ols_plan_status(self._h, reset)
         check(rc, "ols_plan_status")
         return v
@@ -315,11 +317,11 @@ def decode_candidates(records: torch.Tensor, count: int):
     """(f, j, power) numpy arrays of the first min(count, capacity) records
     written by ``Plan.convolve_detect`` (record layout of ols_candidate)."""
     n = min(int(count), records.shape[0])
-    r = records[:n].cpu()
-    j = r[:, 0].numpy().copy()
-    w = r[:, 1].contiguous()
-    f = w.view(torch.int32).view(n, 2)[:, 0].numpy().copy()
-    p = w.view(torch.float32).view(n, 2)[:, 1].numpy().copy()
+    r = np.ascontiguousarray(records[:n].cpu().numpy())
+    j = r[:, 0].copy()
+    w = np.ascontiguousarray(r[:, 1])          # a fresh array whatever n (a [1] column keeps stride 2 in torch)
+    f = w.view(np.int32).reshape(n, 2)[:, 0].copy()
+    p = w.view(np.float32).reshape(n, 2)[:, 1].copy()
     return f, j, p
 
 
@@ -417,6 +419,12 @@ class BatchPlan:
         st, yt = self.pointer_table(ss), self.pointer_table(ys)
         self.launch(st, yt)
         return ys
+
+    def status(self, reset: bool = True) -> int:
+        """OR of the status words of every problem's plan (see Plan.status)."""
+        rc, v = _native.ols_batch_status(self._h, reset)
+        check(rc, "ols_batch_status")
+        return v
 
     def last_launch_count(self) -> int:
         return _native.ols_batch_last_launch_count(self._h)

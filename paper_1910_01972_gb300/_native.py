@@ -72,6 +72,7 @@ SIGNATURES = [
     ("ols_batch_plan_tiles", cint, [ctypes.POINTER(vp), i32, P_i64, P_i32, P_i32, P_i64, P_i32, u32]),
     ("ols_autotune_tiles", cint, [i32, i32, i64, i32, u32, P_i32]),
     ("ols_batch_schedule", cint, [vp, i32, P_i32, P_i64]),
+    ("ols_batch_status", cint, [vp, P_i32, cint]),
 ]
 
 _lib = None
@@ -254,6 +255,12 @@ def ols_batch_schedule(batch, b: int):
     r, n = i32(), i64()
     rc = lib().ols_batch_schedule(batch, b, ctypes.byref(r), ctypes.byref(n))
     return rc, r.value, n.value
+
+
+def ols_batch_status(batch, reset: bool = True):
+    v = i32()
+    rc = lib().ols_batch_status(batch, ctypes.byref(v), int(reset))
+    return rc, v.value
 
 
 def ols_batch_destroy(batch) -> int:

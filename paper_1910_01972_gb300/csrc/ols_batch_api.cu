@@ -207,6 +207,7 @@ int measure_tiles(int32_t M, int32_t F, int64_t N, int block, int sm_count, int3
     d.F = F;
     d.index = 0;
     d.log2N = l;
+    d.status = p->d_status;
     void *hp[2] = {s, y};
     if (e == cudaSuccess) e = cudaMemcpy(dp, &d, sizeof(d), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ptrs, hp, sizeof(hp), cudaMemcpyHostToDevice);
@@ -416,6 +417,7 @@ int ols_batch_plan_tiles(ols_batch_t *out, int32_t B, const int64_t *Ns, const i
             d.F = bt->F[b];
             d.index = b;
             d.log2N = l;
+            d.status = bt->plans[b]->d_status;
             bt->tw_all.tw[l] = bt->plans[b]->tw;
         }
         // tile schedule: tiles per item of each problem, given or tuned per
@@ -521,6 +523,7 @@ int ols_batch_plan_tiles(ols_batch_t *out, int32_t B, const int64_t *Ns, const i
             d.F = bt->F[b];
             d.index = b;
             d.log2N = l;
+            d.status = bt->plans[b]->d_status;
             const int pi = (int)(probs.size() - p0);
             probs.push_back(d);
             const int64_t tiles = (bt->nseg[b] + segs - 1) / segs;
@@ -605,6 +608,19 @@ int ols_convolve_batched(ols_batch_t batch, const void *s_ptrs, const void *y_pt
 }
 
 int ols_batch_last_launch_count(ols_batch_t batch) { return batch ? batch->last_launches : -1; }
+
+int ols_batch_status(ols_batch_t batch, int *status, int reset) {
+    if (!batch || !status) return OLS_ERR_INVALID;
+    int acc = 0;
+    for (ols_plan_t p : batch->plans) {
+        int v = 0;
+        const int rc = ols_plan_status(p, &v, reset);
+        if (rc != OLS_OK) return rc;
+        acc |= v;
+    }
+    *status = acc;
+    return OLS_OK;
+}
 
 int ols_batch_schedule(ols_batch_t batch, int32_t b, int32_t *tiles, int64_t *items) {
     if (!batch || b < 0 || b >= batch->B) return OLS_ERR_INVALID;

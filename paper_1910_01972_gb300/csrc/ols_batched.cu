@@ -70,7 +70,7 @@ ols_batched_kernel(const BatchProblemDev *__restrict__ probs, const int2 *__rest
         const long long nseg = P.nseg;
         const long long seg = (long long)it.y * G::SEGS + slot;
         ols_segment<LOG2N>(s_ptrs[P.index], P.Ns, P.Hk, tw, y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
-                           seg < nseg, bufs, t, xc);
+                           seg < nseg, bufs, t, xc, 0u, CtaBarrier{}, P.status);
     }
 #if OLS_FWD_TW_TMEM
     tmem::fence_before_sync();
@@ -170,13 +170,13 @@ __device__ __forceinline__ void batch_one_tile(const BatchProblemDev &P, int til
         if (fill) tw_tmem_fill<LOG2N, xch>(tw, twt.base, t);
         ols_segment<LOG2N, TWT, true, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, twt, y_ptrs[P.index],
                                                                P.M, P.F, P.L, P.Nout, seg, seg < P.nseg, bufs, t, xc,
-                                                               0u, bar);
+                                                               0u, bar, P.status);
 #else
         (void)tbase;
         (void)fill;
         ols_segment<LOG2N, TwGlobal, false, SegmentBarrier<G::T>>(s_ptrs[P.index], P.Ns, P.Hk, TwGlobal{tw},
                                                                   y_ptrs[P.index], P.M, P.F, P.L, P.Nout, seg,
-                                                                  seg < P.nseg, bufs, t, xc, 0u, bar);
+                                                                  seg < P.nseg, bufs, t, xc, 0u, bar, P.status);
 #endif
     }
 }

@@ -157,6 +157,7 @@ struct BatchProblemDev {
     int M, F;
     int index;            // position in the caller's pointer arrays
     int log2N;            // segment length of this problem
+    int *status;          // the problem's plan status word (bounds checks of OLS_CHECK builds)
 };
 
 // Twiddle tables of every segment length, by log2 N (single-launch batches).

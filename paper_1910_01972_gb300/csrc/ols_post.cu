@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, (PostGeo<LOG2N, MODE>::MINB
 ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
                 const float2 *__restrict__ twg, void *__restrict__ out, int M, int F, long long step,
                 long long nseg, long long Nout, float thr, ols_candidate *__restrict__ cand,
-                unsigned long long *__restrict__ count, long long cap) {
+                unsigned long long *__restrict__ count, long long cap, int *status) {
     using G = Geo<LOG2N>;
     using PG = PostGeo<LOG2N, MODE>;
     extern __shared__ float4 smem_raw[];
@@ -96,7 +96,9 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const int n = k * G::T + t;
-                X[k] = (n >= first && n < lim) ? __ldg(src + k * G::T) : make_float2(0.f, 0.f);
+                const long long i = (active ? start : 0) + n;
+                X[k] = (n >= first && n < lim && in_bounds(i >= 0 && i < Ns, status)) ? __ldg(src + k * G::T)
+                                                                                     : make_float2(0.f, 0.f);
             }
         }
         forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
@@ -109,8 +111,10 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
         const int span = (int)(rem < step ? rem : step);
 
         float4 hn[8];
+        const long long hn_end = (long long)F * (G::N / 2);   // float4 entries of the spectra
 #pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
+        for (int j2 = 0; j2 < 8; ++j2)
+            if (in_bounds(j2 * G::T + t < hn_end, status)) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
         for (int f = 0; f < F; ++f) {
             float2 x[16];
 #if OLS_FWD_TW_TMEM
@@ -128,7 +132,9 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
             if (f + 1 < F) {
                 const float4 *hp = Hk + (size_t)(f + 1) * (G::N / 2) + t;
 #pragma unroll
-                for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+                for (int j2 = 0; j2 < 8; ++j2)
+                    if (in_bounds((long long)(f + 1) * (G::N / 2) + j2 * G::T + t < hn_end, status))
+                        hn[j2] = load_spectrum(hp + j2 * G::T);
             }
             inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
 
@@ -137,7 +143,8 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int n = k * G::T + t;
-                    if ((unsigned)(n - n0) < (unsigned)span) dst[n] = fmaf(x[k].x, x[k].x, x[k].y * x[k].y);
+                    if ((unsigned)(n - n0) < (unsigned)span && in_bounds(j0 - n0 + n >= 0 && j0 - n0 + n < Nout, status))
+                        dst[n] = fmaf(x[k].x, x[k].x, x[k].y * x[k].y);
                 }
             } else if constexpr (MODE == POST_DETECT) {
                 const unsigned lane = threadIdx.x & 31u;
@@ -154,7 +161,7 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
                         base = __shfl_sync(0xffffffffu, base, leader);
                         if (hit) {
                             const unsigned long long i = base + __popc(mask & ((1u << lane) - 1u));
-                            if (i < (unsigned long long)cap) {
+                            if (i < (unsigned long long)cap && in_bounds(j0 + (n - n0) < Nout, status)) {
                                 ols_candidate c;
                                 c.j = j0 + (n - n0);
                                 c.f = f;
@@ -179,7 +186,8 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int n = k * G::T + t;
-                    if ((unsigned)(n - n0) < (unsigned)span) {
+                    if ((unsigned)(n - n0) < (unsigned)span &&
+                        in_bounds(j0 - n0 + n >= 0 && j0 - n0 + n < Nout && n >= 1 && n + 1 < G::N, status)) {
                         const int lo = (n == n_first) ? n : n - 1;
                         const int hi = (n == n_last) ? n : n + 1;
                         const float sc = (lo == n || hi == n) ? 1.f : 0.5f;
@@ -245,7 +253,7 @@ static cudaError_t post_launch_nm(const ols_plan_s &p, const PostArgs &a, cudaSt
     const int grid = fused_grid(LOG2N, nblk, cap);
     ols_post_kernel<LOG2N, MODE><<<grid, G::BLOCK, PG::SMEM, st>>>(
         a.s, a.Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, a.out, p.M, p.F, a.step, a.nseg, a.Nout, a.thr,
-        a.cand, a.count, a.cap);
+        a.cand, a.count, a.cap, p.d_status);
     return cudaGetLastError();
 }
 

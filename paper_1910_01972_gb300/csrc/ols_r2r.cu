@@ -52,7 +52,7 @@ template <int LOG2N>
 __global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, Geo<LOG2N>::MINB)
 ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__restrict__ Hk,
                const float2 *__restrict__ twg, float *__restrict__ y, int M, int F, long long L, long long nseg,
-               long long Nout) {
+               long long Nout, int *status) {
     using G = Geo<LOG2N>;
     extern __shared__ float4 smem_raw[];
     __shared__ uint32_t tbase;
@@ -93,7 +93,11 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
             const float *src = sig + (active ? start : 0) + t;
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                X[k] = make_float2((k * G::T + t < lim) ? __ldg(src + k * G::T) : 0.f, 0.f);
+                X[k] = make_float2(
+                    (k * G::T + t < lim && in_bounds((active ? start : 0) + k * G::T + t < Ns, status))
+                        ? __ldg(src + k * G::T)
+                        : 0.f,
+                    0.f);
         }
         forward_passes<LOG2N, 0>(X, bufs, tw, t, xc);
 #if OLS_FWD_TW_TMEM
@@ -106,8 +110,10 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
         const long long obase = start - lo;
 
         float4 hn[8];
+        const long long hn_end = (long long)Fc * (G::N / 2);   // float4 entries of the paired spectra
 #pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
+        for (int j2 = 0; j2 < 8; ++j2)
+            if (in_bounds(j2 * G::T + t < hn_end, status)) hn[j2] = load_spectrum(Hk + j2 * G::T + t);
         for (int p = 0; p < Fc; ++p) {
             float2 x[16];
 #if OLS_FWD_TW_TMEM
@@ -125,7 +131,9 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
             if (p + 1 < Fc) {
                 const float4 *hp = Hk + (size_t)(p + 1) * (G::N / 2) + t;
 #pragma unroll
-                for (int j2 = 0; j2 < 8; ++j2) hn[j2] = load_spectrum(hp + j2 * G::T);
+                for (int j2 = 0; j2 < 8; ++j2)
+                    if (in_bounds((long long)(p + 1) * (G::N / 2) + j2 * G::T + t < hn_end, status))
+                        hn[j2] = load_spectrum(hp + j2 * G::T);
             }
             inverse_passes<LOG2N, G::NP - 1>(x, bufs, tw, t, xc);
             float *dre = y + (size_t)(2 * p) * (size_t)Nout + obase;
@@ -136,7 +144,8 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int n = k * G::T + t;
-                    const bool ok = (unsigned)(n - lo) < (unsigned)span;
+                    const bool ok = (unsigned)(n - lo) < (unsigned)span &&
+                                    in_bounds(obase + n >= 0 && obase + n < Nout, status);
                     if (ok) dre[n] = x[k].x;
                     if (ok) dim[n] = x[k].y;
                 }
@@ -144,7 +153,8 @@ ols_r2r_kernel(const float *__restrict__ sig, long long Ns, const float4 *__rest
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int n = k * G::T + t;
-                    if ((unsigned)(n - lo) < (unsigned)span) dre[n] = x[k].x;
+                    if ((unsigned)(n - lo) < (unsigned)span && in_bounds(obase + n >= 0 && obase + n < Nout, status))
+                        dre[n] = x[k].x;
                 }
             }
         }
@@ -181,7 +191,7 @@ static cudaError_t r2r_launch_n(const ols_plan_s &p, const float *s, int64_t Ns,
     const int64_t nblk = (nseg + G::SEGS - 1) / G::SEGS;
     const int grid = fused_grid(LOG2N, nblk, p.r2r_grid_cap);
     ols_r2r_kernel<LOG2N><<<grid, G::BLOCK, G::SMEM_TMEM, st>>>(s, Ns, reinterpret_cast<const float4 *>(p.Hk), p.tw, y,
-                                                           p.M, p.F, L, nseg, Nout);
+                                                           p.M, p.F, L, nseg, Nout, p.d_status);
     return cudaGetLastError();
 }
 

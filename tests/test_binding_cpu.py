@@ -55,3 +55,20 @@ def test_autograd_values_resolves_views():
     z = torch.tensor([1 + 2j], dtype=torch.complex64)
     r = autograd._values(z.conj())
     assert not r.is_conj() and r.item() == 1 - 2j
+
+
+@pytest.mark.parametrize("n", [0, 1, 3])
+def test_decode_candidates_any_count(n):
+    """Records laid out as ols_candidate (int64 j; int32 f; float power),
+    decoded for every count, including one record (a [1] column whose torch
+    stride stays 2) and counts above the capacity."""
+    import numpy as np
+    rec = np.zeros(4, dtype=[("j", "<i8"), ("f", "<i4"), ("power", "<f4")])
+    rec["j"] = [10, 2**40, 7, 5]
+    rec["f"] = [3, 0, 31, 2]
+    rec["power"] = [1.5, 2.25, 1e30, 0.0]
+    t = torch.from_numpy(rec.view(np.int64).reshape(4, 2).copy())
+    f, j, p = ols.decode_candidates(t[:3], n)
+    assert list(j) == list(rec["j"][:n]) and list(f) == list(rec["f"][:n]) and list(p) == list(rec["power"][:n])
+    f, j, p = ols.decode_candidates(t[:2], 9)       # count above capacity: the stored records only
+    assert list(j) == [10, 2**40] and list(f) == [3, 0]

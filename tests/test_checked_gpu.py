@@ -1,6 +1,6 @@
 """The bounds-checked debug build (OLS_CHECK=1): the parity edge cases of the
-forward, tensor-core and adjoint kernels run in a child process on that
-build, every global access checked against its buffer; no check may fail
+forward, real-to-real, post-processing, tensor-core, adjoint and batched
+kernels run in a child process on that build, every global access checked against its buffer; no check may fail
 (the plan status words stay 0) and the results keep the parity bounds."""
 import json
 import os
@@ -31,8 +31,11 @@ def test_no_access_fails_its_bounds_check():
     assert r.returncode == 0, r.stderr[-3000:]
     res = json.loads(r.stdout.strip().splitlines()[-1])
     assert res["library"] == "libols_check.so"
-    assert res["cases"] == 18
+    assert res["cases"] == 32
     assert res["status"] == 0, res                 # no failed bounds check, no expired wait
     w = res["worst"]
+    print(json.dumps(res))
     assert w["fwd"] <= 2e-6 and w["tc"] <= 2e-6 and w["ds"] <= 2e-6 and w["dh"] <= 1e-5, w
+    assert w["r2r"] <= 2e-6 and w["power"] <= 4e-6 and w["deriv"] <= 2e-6 and w["batch"] <= 2e-6, json.dumps(res)
+    assert w["detect"] == 0.0, w
     assert res["tc_split_equal"]

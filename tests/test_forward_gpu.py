@@ -1,7 +1,10 @@
 """Parity of the fused FP32 OLS kernel (through the C ABI) with the FP64 oracle.
 
 Tolerance: max over filters of ||y - y_ref||_2 / ||y_ref||_2 <= 2e-6 (FP32
-path against the FP64 direct sum of Eq. 1).  Index bookkeeping (segment
+path against the FP64 direct sum of Eq. 1), the denominator floored at the
+stream's expected norm sqrt(Nout) ||h_f|| rms(s) (oracle.stream_scale): a
+stream of one or two outputs can be near zero by chance, while the FFT's
+rounding error follows the segment's energy.  Index bookkeeping (segment
 starts, discarded samples, the ragged tail) is checked bit-exactly with
 delta filters on integer-valued signals.
 """
@@ -83,7 +86,7 @@ def test_parity_with_oracle(N, M, F, Ns, window):
     y = run(s, h, N)
     y_ref = oracle.conv(s, h)
     assert y.shape == y_ref.shape
-    err = oracle.max_stream_rel_l2(y, y_ref)
+    err = oracle.max_stream_rel_l2(y, y_ref, oracle.stream_scale(s, h, y.shape[1]))
     assert err <= TOL, err
 
 

@@ -281,3 +281,27 @@ def test_post_pins_catch_planted_mistake(name):
             except AssertionError:
                 caught.append(pin.__name__)
         assert caught, "planted mistake %s passed every post-processing pin" % name
+
+
+def test_error_metric_floor():
+    """The parity metric: without a floor it is the per-stream relative L2
+    error; the floor only replaces a denominator below it; stream_scale is
+    the expected stream norm of a white signal (within a few percent on
+    long streams, so the floor leaves their error unchanged)."""
+    g = np.random.Generator(np.random.PCG64(3))
+    y_ref = g.normal(size=(3, 50)) + 1j * g.normal(size=(3, 50))
+    y = y_ref + 1e-3 * (g.normal(size=(3, 50)) + 0j)
+    plain = max(np.linalg.norm(y[f] - y_ref[f]) / np.linalg.norm(y_ref[f]) for f in range(3))
+    assert oracle.max_stream_rel_l2(y, y_ref) == pytest.approx(plain, rel=1e-12)
+    assert oracle.max_stream_rel_l2(y, y_ref, floor=[0.0, 0.0, 0.0]) == pytest.approx(plain, rel=1e-12)
+    big = [1e6] * 3
+    assert oracle.max_stream_rel_l2(y, y_ref, floor=big) == pytest.approx(
+        max(np.linalg.norm(y[f] - y_ref[f]) for f in range(3)) / 1e6, rel=1e-12)
+    Ns, M, F = 200_000, 33, 2
+    s = (g.normal(size=Ns) + 1j * g.normal(size=Ns)).astype(np.complex64)
+    h = (g.normal(size=(F, M)) + 1j * g.normal(size=(F, M))).astype(np.complex64)
+    yr = oracle.conv(s, h)
+    sc = oracle.stream_scale(s, h, Ns - M + 1)
+    assert sc.shape == (F,)
+    for f in range(F):
+        assert np.linalg.norm(yr[f]) == pytest.approx(sc[f], rel=0.05)
