@@ -761,17 +761,39 @@ def run_ours(args):
         y_host = torch.empty((cfg.F, Nout), dtype=torch.complex64, pin_memory=True)
         plan.convolve_host(s_host, y_host)
         torch.cuda.synchronize()
+
+        def d2h_probe(n=3):
+            # one whole-output copy device -> host, individually timed
+            r = []
+            for _ in range(n):
+                e0.record(st)
+                y_host.copy_(y, non_blocking=True)
+                e1.record(st)
+                torch.cuda.synchronize()
+                r.append(round(e0.elapsed_time(e1), 3))
+            return r
+
+        probe_before = d2h_probe()
         if dist is not None:
             dist.barrier()
+        per_call = []
         t0 = time.time()
         e0.record(st)
         for _ in range(args.e2e_steps):
-            plan.convolve_host(s_host, y_host)
+            tc = time.perf_counter()
+            plan.convolve_host(s_host, y_host)      # returns after y_host is complete
+            per_call.append((time.perf_counter() - tc) * 1e3)
         e1.record(st)
         torch.cuda.synchronize()
         t1 = time.time()
         clocks.mark(t0, t1)
         ms_e2e = (t1 - t0) * 1e3 / args.e2e_steps
+        probe_after = d2h_probe()
+        # one more call (outside the timed region) with the library's per-stage events
+        plan.host_timing(True)
+        plan.convolve_host(s_host, y_host)
+        stages = {k: (round(v, 3) if k != "chunks" else v) for k, v in plan.host_stage_ms().items()}
+        plan.host_timing(False)
         if dist is not None:
             t = torch.tensor([ms_e2e], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -800,7 +822,11 @@ def run_ours(args):
         e2e = {"value": world * outputs / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                "steps": args.e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * cfg.F * Nout,
                "path": "ols_convolve_host: pinned host buffers, chunked H2D / kernel / D2H on two streams",
-               "link": link, "frac_of_link_floor": link["floor_ms"] / ms_e2e}
+               "link": link, "frac_of_link_floor": link["floor_ms"] / ms_e2e,
+               "per_call_ms": {"min": round(min(per_call), 3), "median": round(statistics.median(per_call), 3),
+                               "max": round(max(per_call), 3)},
+               "d2h_probe_ms": {"before": probe_before, "after": probe_after},
+               "stages_one_call": stages}
         del y_host, s_host
     others, samples = (None, None)
     if rank == 0 and world == 1 and not args.no_others and not args.ns:

@@ -299,6 +299,27 @@ OLS_API int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, 
                       void *stream);
 
 /*
+ * Stage timing of ols_convolve_host (off by default): with on != 0 every
+ * later ols_convolve_host call on this plan records CUDA events around each
+ * chunk's host->device copy, kernel and device->host copy (four per chunk,
+ * created on first use and kept with the staging buffers).
+ * Errors: INVALID.
+ */
+OLS_API int ols_host_timing(ols_plan_t plan, int on);
+
+/*
+ * The last timed ols_convolve_host call, in device milliseconds: ms[0] the
+ * host->device copies, ms[1] the kernels, ms[2] the device->host copies,
+ * each summed over the chunks (a stage's time includes any wait for a copy
+ * engine or the SMs, so with two streams the sums can exceed the span);
+ * ms[3] the span from the first chunk's start to the last chunk's end;
+ * ms[4] the number of chunks.  ms: host array of 5 doubles.
+ * Errors: INVALID, NOT_READY (timing off, or no call since it was turned on),
+ * CUDA.
+ */
+OLS_API int ols_host_stage_ms(ols_plan_t plan, double *ms);
+
+/*
  * Workspace (bytes) that ols_convolve_backward needs for a signal of Ns
  * samples, given which gradients are wanted (want_ds, want_dh: 0 or 1).
  * May be 0.  Errors: INVALID, UNSUPPORTED (as ols_geometry).

@@ -270,6 +270,17 @@ class Plan:
                                         _stream_ptr(self.device)), "ols_convolve_host")
         return out_host
 
+    def host_timing(self, on: bool = True) -> None:
+        """Record per-stage events in later ``convolve_host`` calls (see host_stage_ms)."""
+        check(_native.ols_host_timing(self._h, on), "ols_host_timing")
+
+    def host_stage_ms(self) -> dict:
+        """Device time of the last timed ``convolve_host`` call: copies in, kernels,
+        copies out (each summed over the chunks), the span, and the chunk count."""
+        rc, ms = _native.ols_host_stage_ms(self._h)
+        check(rc, "ols_host_stage_ms")
+        return {"h2d_ms": ms[0], "kernel_ms": ms[1], "d2h_ms": ms[2], "span_ms": ms[3], "chunks": int(ms[4])}
+
     def backward_workspace(self, Ns: int, want_ds: bool = True, want_dh: bool = True) -> int:
         rc, nb = _native.ols_backward_workspace(self._h, int(Ns), want_ds, want_dh)
         check(rc, "ols_backward_workspace")

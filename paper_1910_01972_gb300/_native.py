@@ -50,6 +50,8 @@ SIGNATURES = [
     ("ols_get_spectra", cint, [vp, vp, vp]),
     ("ols_convolve", cint, [vp, vp, i64, vp, vp]),
     ("ols_convolve_host", cint, [vp, vp, i64, vp, vp]),
+    ("ols_host_timing", cint, [vp, cint]),
+    ("ols_host_stage_ms", cint, [vp, ctypes.POINTER(ctypes.c_double)]),
     ("ols_convolve_split", cint, [vp, vp, vp, i64, vp, vp]),
     ("ols_split_signal", cint, [vp, vp, i64, vp, vp, vp]),
     ("ols_convolve_power", cint, [vp, vp, i64, vp, vp]),
@@ -181,6 +183,16 @@ def ols_convolve_real(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int
 
 def ols_convolve_host(plan, s_ptr: int, Ns: int, y_ptr: int, stream: int) -> int:
     return lib().ols_convolve_host(plan, s_ptr, Ns, y_ptr, stream)
+
+
+def ols_host_timing(plan, on: bool) -> int:
+    return lib().ols_host_timing(plan, int(on))
+
+
+def ols_host_stage_ms(plan):
+    ms = (ctypes.c_double * 5)()
+    rc = lib().ols_host_stage_ms(plan, ms)
+    return rc, list(ms)
 
 
 def ols_backward_workspace(plan, Ns: int, want_ds: bool, want_dh: bool):

@@ -165,6 +165,9 @@ static void free_staging(Staging &s) {
     }
     if (s.ev_user) cudaEventDestroy(s.ev_user);
     s.ev_user = nullptr;
+    for (cudaEvent_t ev : s.tev) cudaEventDestroy(ev);
+    s.tev.clear();
+    s.timed_chunks = 0;
     s.in_cap = s.out_cap = 0;
 }
 
@@ -521,13 +524,27 @@ int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y
     float2 *yh = reinterpret_cast<float2 *>(y_host);
     int launches = 0;
     const int64_t nchunk = (nseg + cseg - 1) / cseg;
+    // stage timing: four events per chunk, created once and kept with the staging
+    st.timed_chunks = 0;
+    const bool timed = st.timing;
+    while (timed && e == cudaSuccess && (int64_t)st.tev.size() < 4 * nchunk) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreate(&ev);
+        if (e == cudaSuccess) st.tev.push_back(ev);
+    }
+    auto mark = [&](int64_t c, int k, cudaStream_t cs) {
+        if (timed && e == cudaSuccess) e = cudaEventRecord(st.tev[(size_t)(4 * c + k)], cs);
+    };
     for (int64_t c = 0; c < nchunk && e == cudaSuccess; ++c) {
         const int b = (int)(c & 1);
         cudaStream_t cs = st.st[b];
         const int64_t o0 = c * cout;                                   // first output of the chunk
         const int64_t nout_c = (Nout - o0) < cout ? (Nout - o0) : cout;
         const int64_t nin_c = nout_c + M - 1;                          // s[o0, o0 + nin_c)
-        e = cudaMemcpyAsync(st.in[b], sh + o0, sizeof(float2) * (size_t)nin_c, cudaMemcpyHostToDevice, cs);
+        mark(c, 0, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(st.in[b], sh + o0, sizeof(float2) * (size_t)nin_c, cudaMemcpyHostToDevice, cs);
+        mark(c, 1, cs);
         int64_t Lc, nsegc, Noutc;
         if (e == cudaSuccess) {
             ols_geometry(plan->N, plan->M, nin_c, &Lc, &nsegc, &Noutc);
@@ -535,16 +552,49 @@ int ols_convolve_host(ols_plan_t plan, const float *s_host, int64_t Ns, float *y
             e = launch_any(*plan, st.in[b], nin_c, st.out[b], Lc, nsegc, Noutc, cs, &l);
             launches += l;
         }
+        mark(c, 2, cs);
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(yh + o0, sizeof(float2) * (size_t)Nout, st.out[b], sizeof(float2) * (size_t)nout_c,
                                   sizeof(float2) * (size_t)nout_c, (size_t)F, cudaMemcpyDeviceToHost, cs);
+        mark(c, 3, cs);
     }
     for (int i = 0; i < 2; ++i) {
         cudaError_t e2 = cudaStreamSynchronize(st.st[i]);
         if (e == cudaSuccess) e = e2;
     }
+    if (timed && e == cudaSuccess) st.timed_chunks = nchunk;
     plan->last_launches = launches;
     return status_of(e);
+}
+
+int ols_host_timing(ols_plan_t plan, int on) {
+    if (!plan) return OLS_ERR_INVALID;
+    plan->stage.timing = on != 0;
+    plan->stage.timed_chunks = 0;
+    return OLS_OK;
+}
+
+int ols_host_stage_ms(ols_plan_t plan, double *ms) {
+    if (!plan || !ms) return OLS_ERR_INVALID;
+    const Staging &st = plan->stage;
+    if (!st.timing || st.timed_chunks < 1) return OLS_ERR_NOT_READY;
+    double sum[3] = {0.0, 0.0, 0.0}, span = 0.0;
+    for (int64_t c = 0; c < st.timed_chunks; ++c) {
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.f;
+            const cudaError_t e = cudaEventElapsedTime(&t, st.tev[(size_t)(4 * c + k)], st.tev[(size_t)(4 * c + k + 1)]);
+            if (e != cudaSuccess) return status_of(e);
+            sum[k] += t;
+        }
+        float t = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&t, st.tev[0], st.tev[(size_t)(4 * c + 3)]);
+        if (e != cudaSuccess) return status_of(e);
+        if (t > span) span = t;
+    }
+    for (int k = 0; k < 3; ++k) ms[k] = sum[k];
+    ms[3] = span;
+    ms[4] = (double)st.timed_chunks;
+    return OLS_OK;
 }
 
 // Workspace of the adjoint: overlap edges of ds (nseg x 2 x (M-1) complex),

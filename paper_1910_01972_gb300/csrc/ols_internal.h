@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "ols.h"
 
@@ -69,6 +70,9 @@ struct Staging {            // device buffers of ols_convolve_host
     int64_t in_cap = 0, out_cap = 0;   // elements per buffer
     cudaStream_t st[2] = {nullptr, nullptr};
     cudaEvent_t ev_user = nullptr, ev_done[2] = {nullptr, nullptr};
+    bool timing = false;               // per-stage events (ols_host_timing)
+    std::vector<cudaEvent_t> tev;      // 4 per chunk: start, after H2D, after the kernel, after D2H
+    int64_t timed_chunks = 0;          // chunks of the last timed call (0: none yet)
 };
 
 // Resident blocks per SM of a kernel that allocates `tmem_cols` TMEM columns

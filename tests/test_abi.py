@@ -110,6 +110,9 @@ def test_null_handles_are_rejected():
     assert L.ols_set_filters(None, None, None) == _native.OLS_ERR_INVALID
     assert L.ols_plan_destroy(None) == 0
     assert L.ols_last_launch_count(None) == -1
+    assert L.ols_host_timing(None, 1) == _native.OLS_ERR_INVALID
+    assert _native.ols_host_stage_ms(None)[0] == _native.OLS_ERR_INVALID
+    assert _native.ols_batch_status(None)[0] == _native.OLS_ERR_INVALID
 
 
 def test_tile_schedule_model_rule_and_argument_checks():

@@ -180,6 +180,36 @@ def test_host_buffer_path_matches_device_path():
     plan.close()
 
 
+def test_host_stage_timing():
+    """Stage timing of the host-buffer path: NOT_READY until a timed call,
+    then per-stage device times for every chunk; the results are unchanged
+    (bit for bit) by the events, and turning it off clears it."""
+    import time
+    M, F, N, Ns = 257, 32, 2048, (1 << 21) + 777
+    s, h = rand_inputs(22, Ns, F, M)
+    plan = Plan(M, F, N)
+    plan.set_filters(to_dev(h))
+    s_pin = torch.from_numpy(s).pin_memory()
+    ref = plan.convolve_host(s_pin)
+    assert _native.ols_host_stage_ms(plan.handle)[0] == _native.OLS_ERR_NOT_READY   # timing off
+    plan.host_timing(True)
+    assert _native.ols_host_stage_ms(plan.handle)[0] == _native.OLS_ERR_NOT_READY   # no timed call yet
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y = plan.convolve_host(s_pin)
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    st = plan.host_stage_ms()
+    assert torch.equal(y, ref)
+    assert st["chunks"] == plan.last_launch_count() > 1
+    assert st["h2d_ms"] > 0 and st["kernel_ms"] > 0 and st["d2h_ms"] > 0
+    assert 0 < st["span_ms"] <= wall_ms
+    # bytes moved out / summed D2H time: a plausible host-link rate (> 1 GB/s)
+    assert 8 * F * (Ns - M + 1) / (st["d2h_ms"] * 1e-3) > 1e9
+    plan.host_timing(False)
+    assert _native.ols_host_stage_ms(plan.handle)[0] == _native.OLS_ERR_NOT_READY
+    plan.close()
+
+
 def test_graph_capture_and_side_stream():
     M, F, N, Ns = 129, 8, 1024, 100_000
     s, h = rand_inputs(3, Ns, F, M)
