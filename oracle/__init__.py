@@ -9,8 +9,9 @@ elements): the valid part of Eq. 1 for a bank of filters (Sec. 3.2 states
 that OLS returns exactly this, whatever the segment length), the adjoint
 of that linear map, the real-to-real form, and the post-processing of the
 output (power, and the derivative read as central differences with
-one-sided ends, Sec. 4.3); ``detect`` only selects from ``power``.  This
-module only compiles the C file and marshals numpy arrays through ctypes.
+one-sided ends, Sec. 4.3), and the peak rule on the power (Sec. 4.4's peak
+finding); ``detect`` and ``peaks`` only select from ``power``.  This module
+only compiles the C file and marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
 
@@ -70,6 +71,8 @@ def _load():
         lib.ols_oracle_derivative.restype = ctypes.c_int
         lib.ols_oracle_derivative_at.argtypes = [i64, vp, i32, i32, vp, i64, vp, vp, vp]
         lib.ols_oracle_derivative_at.restype = ctypes.c_int
+        lib.ols_oracle_peak_mask.argtypes = [i32, i64, vp, ctypes.c_double, vp]
+        lib.ols_oracle_peak_mask.restype = ctypes.c_int
         lib.ols_oracle_threads.argtypes = []
         lib.ols_oracle_threads.restype = ctypes.c_int
         lib.ols_oracle_set_threads.argtypes = [ctypes.c_int]
@@ -217,6 +220,32 @@ def detect(s, h, threshold: float):
     if p.ndim == 1:
         p = p[None, :]
     f, j = np.nonzero(p >= threshold)
+    return f, j, p[f, j]
+
+
+def peak_mask(p, threshold: float) -> np.ndarray:
+    """Peak rule of ``ols_oracle_peak_mask`` on a power array p[F][Nout] (or
+    [Nout]): bool mask of the (f, j) whose power reaches the threshold, is
+    above its left neighbour and at least its right one."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    squeeze = p.ndim == 1
+    if squeeze:
+        p = p[None, :]
+    F, Nout = p.shape
+    m = np.zeros((F, Nout), dtype=np.uint8)
+    if _load().ols_oracle_peak_mask(F, Nout, _ptr(p), float(threshold), _ptr(m)) != 0:
+        raise ValueError("ols_oracle_peak_mask rejected the sizes")
+    m = m.astype(bool)
+    return m[0] if squeeze else m
+
+
+def peaks(s, h, threshold: float):
+    """Peaks of the power of the convolved output (``peak_mask`` of
+    ``power``): the (f, j) and their powers (float64)."""
+    p = power(s, h)
+    if p.ndim == 1:
+        p = p[None, :]
+    f, j = np.nonzero(peak_mask(p, threshold))
     return f, j, p[f, j]
 
 

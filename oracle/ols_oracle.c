@@ -284,6 +284,34 @@ int ols_oracle_derivative(int64_t Ns, const float *s, int32_t M, int32_t F, cons
     return 0;
 }
 
+/*
+ * Peak finding on the power (the further reduction of the output that
+ * Sec. 4.4 names, "peak finding or candidate selection"; the paper gives no
+ * rule).  Reading taken: (f, j) is a peak when its power reaches the
+ * threshold and is a local maximum of its stream, strictly above its left
+ * neighbour and at least its right one, so that a run of equal powers gives
+ * one peak, at its left end:
+ *     p_f[j] >= threshold,  p_f[j] > p_f[j-1] (if j > 0),
+ *     p_f[j] >= p_f[j+1] (if j < Nout-1).
+ * mask[f][j] = 1 for a peak, else 0, for p: [F][Nout].  Returns 0, or -1 on
+ * invalid sizes.
+ */
+int ols_oracle_peak_mask(int32_t F, int64_t Nout, const double *p, double threshold, unsigned char *mask)
+{
+    if (F < 1 || Nout < 1) return -1;
+    for (int32_t f = 0; f < F; ++f) {
+        const double *pf = p + (size_t)f * Nout;
+        unsigned char *mf = mask + (size_t)f * Nout;
+        for (int64_t j = 0; j < Nout; ++j) {
+            int peak = pf[j] >= threshold;
+            if (j > 0 && !(pf[j] > pf[j - 1])) peak = 0;
+            if (j < Nout - 1 && !(pf[j] >= pf[j + 1])) peak = 0;
+            mf[j] = (unsigned char)peak;
+        }
+    }
+    return 0;
+}
+
 /* Selected derivatives: out[i] = d_{fi[i]}[ji[i]].  Returns 0, or -1. */
 int ols_oracle_derivative_at(int64_t Ns, const float *s, int32_t M, int32_t F, const float *h, int64_t n,
                              const int64_t *fi, const int64_t *ji, double *out)

@@ -382,3 +382,56 @@ def pin_power_is_squared_magnitude(power, derivative, conv, seed=33):
 
 POST_PINS = (pin_derivative_is_numpy_gradient, pin_derivative_ramp, pin_derivative_closed_form,
              pin_power_is_squared_magnitude)
+
+
+# -- peak finding (Sec. 4.4), pinned through ``peak_mask(p, threshold)`` ------
+
+def pin_peaks_match_scipy(peak_mask, power, seed=41):
+    """On tie-free powers of random convolutions, the interior peaks are
+    exactly scipy.signal.find_peaks with a height bound (a library routine for
+    local maxima; it never reports the two ends, so those are left out)."""
+    from scipy.signal import find_peaks
+    g = np.random.Generator(np.random.PCG64(seed))
+    s = (g.uniform(-1, 1, 3000) + 1j * g.uniform(-1, 1, 3000)).astype(np.complex64)
+    h = (g.normal(size=(3, 17)) + 1j * g.normal(size=(3, 17))).astype(np.complex64)
+    p = power(s, h)
+    for f in range(p.shape[0]):
+        assert np.unique(p[f]).size == p.shape[1]           # no ties
+        thr = float(np.quantile(p[f], 0.6))
+        m = peak_mask(p[f], thr)
+        ref, _ = find_peaks(p[f], height=thr)
+        assert np.array_equal(np.nonzero(m[1:-1])[0] + 1, ref)
+
+
+def pin_peaks_spike_train(peak_mask, power, M=7):
+    """Delta filters on a spike train (closed form: y_f[j] = s[j + M-1 - d_f],
+    so the powers are the squared spikes): a spike on the first and on the
+    last output of the stream, a spike exactly at the threshold, a pair of
+    equal spikes (one peak, at the left one) and a spike below the
+    threshold."""
+    Nout = 60
+    spikes = {0: 9.0, 10: 4.0, 20: 5.0, 21: 5.0, 33: 3.0, 45: 6.0, Nout - 1: 7.0}
+    thr = 16.0                                            # = 4^2: the spike at 10 sits on it
+    want = {0, 10, 20, 45, Nout - 1}                      # 33 (power 9) is below it
+    for d in (0, M // 2, M - 1):
+        s = np.full(Nout + M - 1, 0.5, np.complex64)      # a floor of power 0.25
+        for j, a in spikes.items():
+            s[j + M - 1 - d] = a
+        h = np.zeros((1, M), np.complex64)
+        h[0, d] = 1
+        p = power(s, h)[0]
+        assert set(np.nonzero(peak_mask(p, thr))[0].tolist()) == want, d
+
+
+def pin_peaks_ramps(peak_mask, power):
+    """A rising power has its only peak on the last output, a falling one on
+    the first; a flat one on the first (the left end of a run of equals)."""
+    n = np.arange(1, 41, dtype=np.float64)
+    for p, j in ((n, 39), (n[::-1].copy(), 0), (np.full(40, 3.0), 0)):
+        assert np.nonzero(peak_mask(p, 0.5))[0].tolist() == [j]
+        assert not peak_mask(p, 1e9).any()
+    one = np.array([2.0])
+    assert peak_mask(one, 2.0).tolist() == [True] and peak_mask(one, 2.5).tolist() == [False]
+
+
+PEAK_PINS = (pin_peaks_match_scipy, pin_peaks_spike_train, pin_peaks_ramps)

@@ -1,5 +1,6 @@
 """The FP64 oracle pinned to the paper and to mathematics (CPU only)."""
 import ctypes
+import importlib.util
 import os
 import shutil
 import subprocess
@@ -305,3 +306,64 @@ def test_error_metric_floor():
     assert sc.shape == (F,)
     for f in range(F):
         assert np.linalg.norm(yr[f]) == pytest.approx(sc[f], rel=0.05)
+
+
+@pytest.mark.parametrize("pin", P.PEAK_PINS)
+def test_oracle_peak_pin(pin):
+    if pin is P.pin_peaks_match_scipy:
+        pytest.importorskip("scipy.signal")
+    pin(oracle.peak_mask, oracle.power)
+
+
+PEAK_MUTANTS = {
+    "peak_left_not_strict": ("if (j > 0 && !(pf[j] > pf[j - 1])) peak = 0;",
+                             "if (j > 0 && !(pf[j] >= pf[j - 1])) peak = 0;"),
+    "peak_right_strict": ("if (j < Nout - 1 && !(pf[j] >= pf[j + 1])) peak = 0;",
+                          "if (j < Nout - 1 && !(pf[j] > pf[j + 1])) peak = 0;"),
+    "peak_threshold_strict": ("int peak = pf[j] >= threshold;", "int peak = pf[j] > threshold;"),
+    "peak_first_output_never": ("if (j > 0 && !(pf[j] > pf[j - 1])) peak = 0;",
+                                "if (j == 0 || !(pf[j] > pf[j - 1])) peak = 0;"),
+    "peak_last_output_never": ("if (j < Nout - 1 && !(pf[j] >= pf[j + 1])) peak = 0;",
+                               "if (j == Nout - 1 || !(pf[j] >= pf[j + 1])) peak = 0;"),
+    "peak_minimum": ("if (j > 0 && !(pf[j] > pf[j - 1])) peak = 0;\n            "
+                     "if (j < Nout - 1 && !(pf[j] >= pf[j + 1])) peak = 0;",
+                     "if (j > 0 && !(pf[j] < pf[j - 1])) peak = 0;\n            "
+                     "if (j < Nout - 1 && !(pf[j] <= pf[j + 1])) peak = 0;"),
+}
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(PEAK_MUTANTS))
+def test_peak_pins_catch_planted_mistake(name):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "ols_oracle.c")).read()
+    old, new = PEAK_MUTANTS[name]
+    assert src.count(old) == 1, "mutation anchor not unique: " + name
+    with tempfile.TemporaryDirectory() as d:
+        cpath = os.path.join(d, "mut.c")
+        with open(cpath, "w") as fh:
+            fh.write(src.replace(old, new))
+        so = os.path.join(d, "libmut.so")
+        subprocess.run(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                        "-std=c11", "-o", so, cpath], check=True)
+        lib = ctypes.CDLL(so)
+        lib.ols_oracle_peak_mask.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                             ctypes.c_void_p]
+        lib.ols_oracle_peak_mask.restype = ctypes.c_int
+
+        def mask(p, thr):
+            p = np.ascontiguousarray(p, dtype=np.float64)
+            sq = p.ndim == 1
+            p2 = p[None, :] if sq else p
+            m = np.zeros(p2.shape, np.uint8)
+            assert lib.ols_oracle_peak_mask(p2.shape[0], p2.shape[1], p2.ctypes.data, float(thr), m.ctypes.data) == 0
+            return m.astype(bool)[0] if sq else m.astype(bool)
+
+        caught = []
+        for pin in P.PEAK_PINS:
+            if pin is P.pin_peaks_match_scipy and importlib.util.find_spec("scipy") is None:
+                continue
+            try:
+                pin(mask, oracle.power)
+            except AssertionError:
+                caught.append(pin.__name__)
+        assert caught, "planted mistake %s passed every peak pin" % name
