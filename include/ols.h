@@ -270,6 +270,24 @@ OLS_API int ols_convolve_detect(ols_plan_t plan, const float *s, int64_t Ns, flo
                                 void *stream);
 
 /*
+ * Peak finding on the power of the convolved output (the further reduction
+ * before the output leaves the GPU that Sec. 4.4 names; the paper gives no
+ * rule): every (f, j) with
+ *   p_f[j] >= threshold,  p_f[j] > p_f[j-1] (j > 0),  p_f[j] >= p_f[j+1] (j < Nout-1),
+ * p = |y|^2, so a run of equal powers gives one peak, at its left end.
+ * Records, capacity and count as ols_convolve_detect (no particular order;
+ * *count zeroed by the call; may exceed capacity).  Each segment advances by
+ * L-2 outputs like the derivative's, so the neighbours of every output it
+ * reports are its own unaliased samples, exchanged in shared memory.  The
+ * comparisons are taken in FP32 on the kernel's powers.
+ * Errors: INVALID (pointers, Ns < M, capacity < 0), UNSUPPORTED (not an FP32
+ * complex plan, or N - M + 1 < 3), NOT_READY, CUDA.
+ */
+OLS_API int ols_convolve_peaks(ols_plan_t plan, const float *s, int64_t Ns, float threshold,
+                               ols_candidate *cand, int64_t capacity, unsigned long long *count,
+                               void *stream);
+
+/*
  * Numerical derivative of the convolved output along j (the paper's
  * non-local post-processing example, Sec. 4.3; the paper gives no formula,
  * this is the central difference with one-sided ends):

@@ -212,6 +212,18 @@ class Plan:
               "ols_convolve_detect")
         return rec, cnt
 
+    def convolve_peaks(self, s: torch.Tensor, threshold: float, capacity: int):
+        """Peaks of the power |y_f[j]|^2: at least ``threshold``, above the power
+        of j-1 and at least that of j+1.  Returns (records, count) as
+        ``convolve_detect``."""
+        s, _ = self._signal(s)
+        rec = torch.empty((max(int(capacity), 1), 2), dtype=torch.int64, device=self.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        check(_native.ols_convolve_peaks(self._h, s.data_ptr(), s.shape[0], float(threshold), rec.data_ptr(),
+                                         int(capacity), cnt.data_ptr(), _stream_ptr(self.device)),
+              "ols_convolve_peaks")
+        return rec, cnt
+
     def convolve_derivative(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """Derivative of the convolved output along j (central differences,
         one-sided at the ends): s [Ns] -> d [F][Ns-M+1] complex64."""

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("ols_split_signal", cint, [vp, vp, i64, vp, vp, vp]),
     ("ols_convolve_power", cint, [vp, vp, i64, vp, vp]),
     ("ols_convolve_detect", cint, [vp, vp, i64, ctypes.c_float, vp, i64, vp, vp]),
+    ("ols_convolve_peaks", cint, [vp, vp, i64, ctypes.c_float, vp, i64, vp, vp]),
     ("ols_convolve_derivative", cint, [vp, vp, i64, vp, vp]),
     ("ols_set_filters_real", cint, [vp, vp, vp]),
     ("ols_convolve_real", cint, [vp, vp, i64, vp, vp]),
@@ -167,6 +168,11 @@ def ols_convolve_power(plan, s_ptr: int, Ns: int, p_ptr: int, stream: int) -> in
 def ols_convolve_detect(plan, s_ptr: int, Ns: int, threshold: float, cand_ptr, capacity: int, count_ptr: int,
                         stream: int) -> int:
     return lib().ols_convolve_detect(plan, s_ptr, Ns, threshold, cand_ptr, capacity, count_ptr, stream)
+
+
+def ols_convolve_peaks(plan, s_ptr: int, Ns: int, threshold: float, cand_ptr, capacity: int, count_ptr: int,
+                        stream: int) -> int:
+    return lib().ols_convolve_peaks(plan, s_ptr, Ns, threshold, cand_ptr, capacity, count_ptr, stream)
 
 
 def ols_convolve_derivative(plan, s_ptr: int, Ns: int, d_ptr: int, stream: int) -> int:

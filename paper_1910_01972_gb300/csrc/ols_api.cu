@@ -453,6 +453,27 @@ int ols_convolve_detect(ols_plan_t plan, const float *s, int64_t Ns, float thres
     return status_of(e);
 }
 
+int ols_convolve_peaks(ols_plan_t plan, const float *s, int64_t Ns, float threshold, ols_candidate *cand,
+                       int64_t capacity, unsigned long long *count, void *stream) {
+    if (!count || ((uintptr_t)count & 7u) || capacity < 0 || (capacity > 0 && (!cand || !aligned8(cand))))
+        return OLS_ERR_INVALID;
+    PostArgs a;
+    int rc = post_common(plan, s, Ns, &a);
+    if (rc != OLS_OK) return rc;
+    if (a.step < 3) return OLS_ERR_UNSUPPORTED;     // segments laid out like the derivative's
+    a.mode = POST_PEAK;
+    a.step -= 2;
+    a.nseg = (a.Nout + a.step - 1) / a.step;
+    a.thr = threshold;
+    a.cand = cand;
+    a.count = count;
+    a.cap = capacity;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = post_launch(*plan, a, (cudaStream_t)stream);
+    plan->last_launches = 1;
+    return status_of(e);
+}
+
 int ols_convolve_derivative(ols_plan_t plan, const float *s, int64_t Ns, float *d, void *stream) {
     if (!d || !aligned8(d)) return OLS_ERR_INVALID;
     PostArgs a;

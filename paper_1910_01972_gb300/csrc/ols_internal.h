@@ -132,7 +132,7 @@ struct ols_plan_s {
     int tc_split_grid_cap = 0;   // the same for its pre-split-input form
     long long tc_wait_limit = 0; // polls per in-loop mbarrier wait of the tensor-core kernel
     bool tc_wait_never = false;  // test switch: in-loop waits watch an mbarrier nothing arrives on
-    int post_grid_cap[3] = {0, 0, 0};  // post-processing kernels (power, detect, derivative)
+    int post_grid_cap[4] = {0, 0, 0, 0};  // post-processing kernels (power, detect, derivative, peaks)
     // real-to-real plans (OLS_FLAG_R2R)
     float2 *hpack = nullptr;     // [ceil(F/2)][M] paired real filters h_{2p} + i h_{2p+1}
     int r2r_grid_cap = 0;
@@ -191,7 +191,7 @@ struct BatchGroup {
 };
 
 // Fused OLS with post-processing of the output (ols_post.cu).
-enum PostMode { POST_POWER = 0, POST_DETECT = 1, POST_DERIV = 2 };
+enum PostMode { POST_POWER = 0, POST_DETECT = 1, POST_DERIV = 2, POST_PEAK = 3 };
 struct PostArgs {
     int mode;
     const float2 *s;

@@ -17,6 +17,14 @@
 //   output early, so every derivative it writes has both neighbours among
 //   its own unaliased samples (the "immediate neighbourhood" of Sec. 4.3);
 //   the neighbours are exchanged through a shared-memory buffer of their own.
+// * PEAK    (non-local + selection) the peaks of the power (Sec. 4.4's peak
+//   finding): (f, j) whose power reaches the threshold, is above the power of
+//   j - 1 and at least that of j + 1 (no neighbour at the two ends of the
+//   stream), appended like DETECT; segments laid out like DERIV.  Candidates
+//   are rare, so a warp fetches neighbour powers (warp shuffles) only when
+//   one of its lanes reaches the threshold; in segments of several warps each
+//   warp's first and last thread also publish their 16 powers in a small
+//   shared buffer for the neighbouring warps.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -29,8 +37,13 @@ namespace ols {
 template <int LOG2N, int MODE>
 struct PostGeo {
     using G = Geo<LOG2N>;
-    static constexpr int BUFS = G::XBUFS + (MODE == POST_DERIV ? 1 : 0);
-    static constexpr size_t SMEM_USED = sizeof(float2) * (size_t)(G::SEGS * BUFS * G::PADN);
+    // the modes that read the neighbours j - 1 and j + 1 of an output
+    static constexpr bool NEIGH = MODE == POST_DERIV || MODE == POST_PEAK;
+    // per segment (float2 units): the exchange buffers; DERIV's neighbourhood
+    // buffer; PEAK's warp-edge powers [2][T/32][16] floats (segments of several warps)
+    static constexpr int EDGE = (MODE == POST_PEAK && G::T > 32) ? (G::T / 32) * 16 : 0;
+    static constexpr int SLOT = G::XBUFS * G::PADN + (MODE == POST_DERIV ? G::PADN : 0) + EDGE;
+    static constexpr size_t SMEM_USED = sizeof(float2) * (size_t)(G::SEGS * SLOT);
     // requested: at least enough that no more blocks fit on an SM (228 KB)
     // than TMEM can serve, so a block's tcgen05.alloc never waits
     static constexpr size_t SMEM = !OLS_FWD_TW_TMEM ? SMEM_USED
@@ -41,6 +54,56 @@ struct PostGeo {
     // fewer per SM keeps it free of register spills
     static constexpr int MINB = (MODE == POST_DERIV && G::MINB > 1) ? G::MINB - 1 : G::MINB;
 };
+
+// The peak test of one output with a candidate power pk (called by whole warps,
+// only when some lane has a candidate: it stays out of the common path's
+// register allocation).  Neighbours n - 1 and n + 1 of output n = k T + t are
+// register k of threads t - 1 and t + 1: rotating shuffles within the W
+// threads of the segment in a warp, whose wrap-around carries `up` (register
+// k - 1 of thread T - 1, for thread 0) and `dn` (register k + 1 of thread 0,
+// for thread T - 1); in segments of several warps, the threads at a warp's
+// edge read the neighbouring warp's powers from `edge` instead.
+template <int T>
+__device__ __noinline__ bool peak_test(bool hit, float pk, float up, float dn, int t, int k, bool first, bool last,
+                                       const float *edge) {
+    constexpr int W = T < 32 ? T : 32;
+    const int gl = t % W;
+    float prv = __shfl_sync(0xffffffffu, up, gl == 0 ? W - 1 : gl - 1, W);
+    float nxt = __shfl_sync(0xffffffffu, dn, gl == W - 1 ? 0 : gl + 1, W);
+    if constexpr (T > 32) {
+        const int w = t / 32, nw = T / 32;
+        if (gl == 0) prv = w > 0 ? edge[(nw + w - 1) * 16 + k] : edge[(2 * nw - 1) * 16 + (k > 0 ? k - 1 : 0)];
+        if (gl == W - 1) nxt = w < nw - 1 ? edge[(w + 1) * 16 + k] : edge[k < 15 ? k + 1 : 15];
+    }
+    if (hit && !first) hit = pk > prv;
+    if (hit && !last) hit = pk >= nxt;
+    return hit;
+}
+
+// Append candidate (j, f, power) for every lane with `hit`: one atomic per
+// warp (warp-aggregated); records past `cap` are dropped, the count is kept.
+__device__ __forceinline__ void append_candidates(bool hit, long long j, int f, float pw, ols_candidate *cand,
+                                                  unsigned long long *count, long long cap, long long Nout,
+                                                  int *status) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (mask) {
+        unsigned long long base = 0;
+        const unsigned leader = __ffs(mask) - 1;
+        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (hit) {
+            const unsigned long long i = base + __popc(mask & ((1u << lane) - 1u));
+            if (i < (unsigned long long)cap && in_bounds(j < Nout, status)) {
+                ols_candidate c;
+                c.j = j;
+                c.f = f;
+                c.power = pw;
+                cand[i] = c;
+            }
+        }
+    }
+}
 
 template <int LOG2N, int MODE>
 __global__ void __launch_bounds__(Geo<LOG2N>::BLOCK, (PostGeo<LOG2N, MODE>::MINB))
@@ -55,8 +118,8 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
     float2 *smem = reinterpret_cast<float2 *>(smem_raw);
     const int slot = threadIdx.x / G::T;
     const int t = threadIdx.x % G::T;
-    float2 *bufs = smem + slot * PG::BUFS * G::PADN;
-    float2 *dbuf = bufs + G::XBUFS * G::PADN;        // DERIV: the output's neighbourhood
+    float2 *bufs = smem + slot * PG::SLOT;
+    float2 *dbuf = bufs + G::XBUFS * G::PADN;        // DERIV: the output's neighbourhood; PEAK: warp edges
 #if OLS_FWD_TW_TMEM
     // the forward kernel's TMEM layout: twiddles, then the segment spectrum (columns 96..127)
     if (threadIdx.x < 32) tmem::alloc(&tbase, G::TMEM_COLS);
@@ -76,8 +139,8 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
     const TwGlobal tw{twg};
 #endif
     // circular position of a segment's first output, and its input offset
-    const int n0 = MODE == POST_DERIV ? M : M - 1;
-    const long long off = MODE == POST_DERIV ? -1 : 0;
+    const int n0 = PG::NEIGH ? M : M - 1;
+    const long long off = PG::NEIGH ? -1 : 0;
     int xc = 0;
     const long long nblk = (nseg + G::SEGS - 1) / G::SEGS;
     for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
@@ -147,29 +210,43 @@ ols_post_kernel(const float2 *__restrict__ sig, long long Ns, const float4 *__re
                         dst[n] = fmaf(x[k].x, x[k].x, x[k].y * x[k].y);
                 }
             } else if constexpr (MODE == POST_DETECT) {
-                const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int n = k * G::T + t;
                     const float p = fmaf(x[k].x, x[k].x, x[k].y * x[k].y);
                     const bool hit = (unsigned)(n - n0) < (unsigned)span && p >= thr;
-                    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-                    if (mask) {
-                        unsigned long long base = 0;
-                        const unsigned leader = __ffs(mask) - 1;
-                        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
-                        base = __shfl_sync(0xffffffffu, base, leader);
-                        if (hit) {
-                            const unsigned long long i = base + __popc(mask & ((1u << lane) - 1u));
-                            if (i < (unsigned long long)cap && in_bounds(j0 + (n - n0) < Nout, status)) {
-                                ols_candidate c;
-                                c.j = j0 + (n - n0);
-                                c.f = f;
-                                c.power = p;
-                                cand[i] = c;
-                            }
-                        }
+                    append_candidates(hit, j0 + (n - n0), f, p, cand, count, cap, Nout, status);
+                }
+            } else if constexpr (MODE == POST_PEAK) {
+                constexpr int W = G::T < 32 ? G::T : 32;          // threads of the segment in one warp
+                const int gl = t % W;
+                float pw[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) pw[k] = fmaf(x[k].x, x[k].x, x[k].y * x[k].y);
+                // segments of several warps: first[w][k] at edge[w * 16 + k], last[w][k] after them
+                float *edge = reinterpret_cast<float *>(dbuf);
+                if constexpr (PG::EDGE > 0) {
+                    if (gl == 0 || gl == W - 1) {
+                        float4 *e = reinterpret_cast<float4 *>(edge + ((gl == 0 ? 0 : G::T / 32) + t / 32) * 16);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            e[q] = make_float4(pw[4 * q], pw[4 * q + 1], pw[4 * q + 2], pw[4 * q + 3]);
                     }
+                    __syncthreads();
+                }
+                // circular positions of outputs j = 0 and j = Nout-1 (one neighbour only), if in this segment
+                const int n_first = j0 == 0 ? n0 : -2;
+                const int n_last = (rem <= step) ? (int)(rem - 1) + n0 : -2;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int n = k * G::T + t;
+                    bool hit = (unsigned)(n - n0) < (unsigned)span && pw[k] >= thr &&
+                               in_bounds(n >= 1 && n + 1 < G::N, status);
+                    if (__any_sync(0xffffffffu, hit))
+                        hit = peak_test<G::T>(hit, pw[k], (gl == W - 1) ? pw[k > 0 ? k - 1 : 0] : pw[k],
+                                              (gl == 0) ? pw[k < 15 ? k + 1 : 15] : pw[k], t, k, n == n_first,
+                                              n == n_last, edge);
+                    append_candidates(hit, j0 + (n - n0), f, pw[k], cand, count, cap, Nout, status);
                 }
             } else {
                 // write y (circular order) to the neighbourhood buffer, padded q -> q + q/16
@@ -229,6 +306,7 @@ static cudaError_t post_prepare_n(ols_plan_s &p) {
     cudaError_t e = post_prepare_nm<LOG2N, POST_POWER>(p);
     if (e == cudaSuccess) e = post_prepare_nm<LOG2N, POST_DETECT>(p);
     if (e == cudaSuccess) e = post_prepare_nm<LOG2N, POST_DERIV>(p);
+    if (e == cudaSuccess) e = post_prepare_nm<LOG2N, POST_PEAK>(p);
     return e;
 }
 
@@ -263,6 +341,7 @@ static cudaError_t post_launch_n(const ols_plan_s &p, const PostArgs &a, cudaStr
         case POST_POWER: return post_launch_nm<LOG2N, POST_POWER>(p, a, st);
         case POST_DETECT: return post_launch_nm<LOG2N, POST_DETECT>(p, a, st);
         case POST_DERIV: return post_launch_nm<LOG2N, POST_DERIV>(p, a, st);
+        case POST_PEAK: return post_launch_nm<LOG2N, POST_PEAK>(p, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -81,7 +81,7 @@ def main():
         note("dh", oracle.max_stream_rel_l2(dh.cpu().numpy(), dh_ref), (N, M, F, Ns))
         out["cases"] += 1
         p.close()
-    worst.update({"r2r": 0.0, "power": 0.0, "deriv": 0.0, "detect": 0.0, "batch": 0.0})
+    worst.update({"r2r": 0.0, "power": 0.0, "deriv": 0.0, "detect": 0.0, "peaks": 0.0, "batch": 0.0})
     for N, M, F, Ns in R2R:
         g = np.random.Generator(np.random.PCG64(13 * N + M + F))
         s, h = synth.real_signal(g, Ns), synth.real_filters(g, F, M)
@@ -116,6 +116,18 @@ def main():
         ok = int(np.sum(p_ref >= thr + band)) <= count <= int(np.sum(p_ref >= thr - band))
         ok = ok and bool(np.all(p_ref[fi, ji] >= thr - band))
         note("detect", 0.0 if ok else 1.0, (N, M, F, Ns))
+        if N - M + 1 >= 3:                                   # peaks: the L-2 layout
+            rec, cnt = p.convolve_peaks(sd, thr, capacity=64)
+            torch.cuda.synchronize()
+            out["status"] |= p.status()
+            count = int(cnt.item())
+            fi, ji, _ = decode_candidates(rec, count)
+            left = np.pad(p_ref[:, :-1], ((0, 0), (1, 0)), constant_values=-np.inf)
+            right = np.pad(p_ref[:, 1:], ((0, 0), (0, 1)), constant_values=-np.inf)
+            may = (p_ref >= thr * (1 - 2e-5)) & (p_ref >= left * (1 - 2e-5)) & (p_ref >= right * (1 - 2e-5))
+            must = (p_ref >= thr * (1 + 2e-5)) & (p_ref > left * (1 + 2e-5)) & (p_ref >= right * (1 + 2e-5))
+            ok = int(must.sum()) <= count <= int(may.sum()) and bool(np.all(may[fi, ji]))
+            note("peaks", 0.0 if ok else 1.0, (N, M, F, Ns))
         out["cases"] += 1
         p.close()
     g = np.random.Generator(np.random.PCG64(19))

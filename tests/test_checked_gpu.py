@@ -37,5 +37,5 @@ def test_no_access_fails_its_bounds_check():
     print(json.dumps(res))
     assert w["fwd"] <= 2e-6 and w["tc"] <= 2e-6 and w["ds"] <= 2e-6 and w["dh"] <= 1e-5, w
     assert w["r2r"] <= 2e-6 and w["power"] <= 4e-6 and w["deriv"] <= 2e-6 and w["batch"] <= 2e-6, json.dumps(res)
-    assert w["detect"] == 0.0, w
+    assert w["detect"] == 0.0 and w["peaks"] == 0.0, w
     assert res["tc_split_equal"]

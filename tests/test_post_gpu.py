@@ -208,3 +208,147 @@ def test_post_entry_points_check_arguments():
         _native.OLS_ERR_UNSUPPORTED
     r.close()
     torch.cuda.synchronize()
+
+
+# -- peak finding (Sec. 4.4) -------------------------------------------------
+# The kernel decides in FP32 on its own powers, the oracle in FP64: a
+# candidate must be reported when every comparison of the rule holds with a
+# relative margin BAND, and may be reported when each holds within it.
+BAND = 2e-5
+
+
+def peak_bands(p, thr):
+    """(must, may) bool masks of the peak rule on p [F][Nout] (numpy or torch)
+    with every comparison taken with / without a relative margin BAND."""
+    mod = torch if isinstance(p, torch.Tensor) else np
+    inf = float("inf")
+    if mod is torch:
+        left = torch.nn.functional.pad(p[:, :-1], (1, 0), value=-inf)
+        right = torch.nn.functional.pad(p[:, 1:], (0, 1), value=-inf)
+    else:
+        left = np.pad(p[:, :-1], ((0, 0), (1, 0)), constant_values=-inf)
+        right = np.pad(p[:, 1:], ((0, 0), (0, 1)), constant_values=-inf)
+    must = (p >= thr * (1 + BAND)) & (p > left * (1 + BAND)) & (p >= right * (1 + BAND))
+    may = (p >= thr * (1 - BAND)) & (p >= left * (1 - BAND)) & (p >= right * (1 - BAND))
+    return must, may
+
+
+PEAK_CASES = [(2048, 257, 8, 40_000), (256, 33, 3, 10_000), (256, 254, 2, 3_000), (512, 1, 2, 5_000),
+              (1024, 129, 5, 50_001), (4096, 512, 3, 70_000), (8192, 1025, 2, 100_000),
+              (1024, 100, 3, 1_000), (2048, 257, 2, 257)]
+
+
+@pytest.mark.parametrize("N,M,F,Ns", PEAK_CASES)
+def test_peaks_match_oracle(N, M, F, Ns):
+    s, h = rand_inputs(N + 9 * M + F, Ns, F, M)
+    p_ref = oracle.power(s, h)
+    thr = float(np.quantile(p_ref, 0.9)) if p_ref.size > 10 else float(p_ref.min())
+    plan = make_plan(h, N)
+    rec, cnt = plan.convolve_peaks(to_dev(s), thr, capacity=p_ref.size + 1)
+    torch.cuda.synchronize()
+    count = int(cnt.item())
+    f, j, pw = decode_candidates(rec, count)
+    plan.close()
+    got = set(zip(f.tolist(), j.tolist()))
+    assert len(got) == count                                   # no duplicates, nothing dropped
+    must, may = peak_bands(p_ref, thr)
+    must = set(zip(*[a.tolist() for a in np.nonzero(must)]))
+    may = set(zip(*[a.tolist() for a in np.nonzero(may)]))
+    assert must <= got <= may
+    assert count >= 1 and np.all(np.abs(pw - p_ref[f, j]) <= TOL_P * p_ref[f, j])
+    exact = set(zip(*[a.tolist() for a in np.nonzero(oracle.peak_mask(p_ref, thr))]))
+    assert must <= exact <= may                                # the bands bracket the exact rule
+
+
+@pytest.mark.parametrize("N", [256, 2048, 8192])
+@pytest.mark.parametrize("M", [1, 37, 250])
+def test_peaks_spike_train_exact(N, M):
+    """Delta filters on a tie-free integer spike train: the peaks are known in
+    closed form, including spikes on the first and last output and spikes on
+    every segment boundary of the L-2 layout."""
+    L = N - M + 1
+    if L < 3:
+        pytest.skip("needs N - M + 1 >= 3")
+    Nout = 3 * N + 123
+    g = np.random.Generator(np.random.PCG64(N + M))
+    pos = np.unique(np.concatenate([[0, Nout - 1], np.arange(1, 8) * (L - 2), np.arange(1, 8) * (L - 2) - 1,
+                                    g.integers(0, Nout, 40)]))
+    pos = pos[(pos >= 0) & (pos < Nout)]
+    pos = pos[np.concatenate([[True], np.diff(pos) > 1])]      # no two adjacent spikes
+    for d in sorted({0, M // 2, M - 1}):
+        base = (1 + (np.arange(Nout) % 7)) * 0.25                # small, non-increasing runs never tie a spike
+        amp = 10.0 + np.arange(pos.size)                          # distinct spikes, powers 100 and up
+        y = base.astype(np.complex64)
+        y[pos] = amp
+        s = np.zeros(Nout + M - 1, np.complex64)
+        s[np.arange(Nout) + M - 1 - d] = y
+        h = np.zeros((1, M), np.complex64)
+        h[0, d] = 1
+        plan = make_plan(h, N)
+        rec, cnt = plan.convolve_peaks(to_dev(s), 50.0, capacity=4 * pos.size)
+        torch.cuda.synchronize()
+        f, j, pw = decode_candidates(rec, int(cnt.item()))
+        plan.close()
+        assert sorted(j.tolist()) == pos.tolist(), (N, M, d)
+        assert np.array_equal(np.sort(pw), np.sort((amp * amp).astype(np.float32))) or \
+            np.allclose(np.sort(pw), np.sort(amp * amp), rtol=1e-5)
+
+
+def test_peaks_capacity_and_arguments():
+    M, F, N, Ns = 65, 3, 512, 20_000
+    s, h = rand_inputs(43, Ns, F, M)
+    p_ref = oracle.power(s, h)
+    thr = float(np.quantile(p_ref, 0.5))
+    plan = make_plan(h, N)
+    rec, cnt = plan.convolve_peaks(to_dev(s), thr, capacity=50)
+    torch.cuda.synchronize()
+    must, may = peak_bands(p_ref, thr)
+    count = int(cnt.item())
+    assert int(must.sum()) <= count <= int(may.sum()) and count > 50
+    f, j, pw = decode_candidates(rec, count)
+    assert f.size == 50 and np.all(may[f, j])
+    st = torch.cuda.current_stream().cuda_stream
+    sd = to_dev(s)
+    assert _native.ols_convolve_peaks(plan.handle, sd.data_ptr(), Ns, thr, rec.data_ptr(), -1, cnt.data_ptr(),
+                                      st) == _native.OLS_ERR_INVALID
+    assert _native.ols_convolve_peaks(plan.handle, sd.data_ptr(), M - 1, thr, rec.data_ptr(), 5, cnt.data_ptr(),
+                                      st) == _native.OLS_ERR_INVALID
+    plan.close()
+    p2 = Plan(255, 1, 256)                                        # L = 2: no room for the L-2 layout
+    p2.set_filters(to_dev(np.ones((1, 255), np.complex64)))
+    assert _native.ols_convolve_peaks(p2.handle, sd.data_ptr(), 300, 1.0, rec.data_ptr(), 5, cnt.data_ptr(),
+                                      st) == _native.OLS_ERR_UNSUPPORTED
+    p2.close()
+
+
+def test_peaks_full_size_bank():
+    """The benchmark's filter bank (Ns = 2^23, F = 32, M = 257, N = 2048): the
+    peaks bracket those of the kernel's own power array (pinned to the oracle
+    by the power tests), and each reported power matches the oracle's."""
+    cfg = synth.PLAIN_BANK
+    s, h = synth.plain_inputs(cfg)
+    plan = make_plan(h, cfg.N)
+    sd = to_dev(s)
+    p = plan.convolve_power(sd)
+    thr = float(torch.quantile(p[0, : 1 << 20].float(), 0.999).item())
+    must, may = peak_bands(p, thr)
+    del p
+    n_must, n_may = int(must.sum().item()), int(may.sum().item())
+    rec, cnt = plan.convolve_peaks(sd, thr, capacity=n_may + 16)
+    torch.cuda.synchronize()
+    count = int(cnt.item())
+    assert n_must <= count <= n_may
+    j = rec[:count, 0].clone()
+    w = torch.empty(count, dtype=torch.int64, device=rec.device)
+    w.copy_(rec[:count, 1])                                      # a fresh contiguous column
+    f = w.view(torch.int32).view(count, 2)[:, 0].long()
+    assert bool(may[f, j].all())
+    got = torch.zeros_like(must)
+    got[f, j] = True
+    assert int(got.sum().item()) == count                       # no duplicates
+    assert bool((got | ~must).all())                            # every sure peak reported
+    del must, may, got
+    fi, ji, pw = decode_candidates(rec, min(count, 3000))
+    ref = oracle.power_at(s, h, fi, ji)
+    assert np.all(np.abs(pw - ref) <= TOL_P * ref)
+    plan.close()
