@@ -97,7 +97,10 @@ typedef struct ols_batch_s *ols_batch_t;
 /* Human-readable name of a status code (static storage; never NULL). */
 OLS_API const char *ols_status_string(int status);
 
-/* Library ABI version (major*100 + minor). */
+/* Library ABI version (major*100 + minor): 101.  1.1 added the split-storage
+ * input of the tensor-core forms, batch tile schedules and status, stage
+ * timing of the host-buffer path and peak finding; every 1.0 call is
+ * unchanged. */
 OLS_API int ols_version(void);
 
 /*

@@ -206,7 +206,7 @@ const char *ols_status_string(int status) {
     }
 }
 
-int ols_version(void) { return 100; }
+int ols_version(void) { return 101; }   // 1.1: split-storage input, batch tile schedules and status, host stage timing, peaks
 
 int ols_geometry(int64_t N, int32_t M, int64_t Ns, int64_t *L, int64_t *nseg, int64_t *Nout) {
     if (M < 1 || Ns < M) return OLS_ERR_INVALID;
