@@ -844,7 +844,7 @@ def run_ours(args):
                "path": "ols_convolve_host: pinned host buffers, chunked H2D / kernel / D2H on two streams",
                "link": link, "frac_of_link_floor": link["floor_ms"] / ms_e2e,
                "per_call_ms": {"min": round(min(per_call), 3), "median": round(statistics.median(per_call), 3),
-                               "max": round(max(per_call), 3)},
+                               "max": round(max(per_call), 3), "all": [round(x, 2) for x in per_call]},
                "d2h_probe_ms": {"before": probe_before, "after": probe_after},
                "stages_one_call": stages}
         del y_host, s_host
