@@ -48,6 +48,7 @@ def test_batched_matches_oracle_and_plain_calls(per_n):
     ys = bp.convolve(sd)
     torch.cuda.synchronize()
     assert bp.last_launch_count() == (len(set(SMALL["N"])) if per_n else 1)
+    assert bp.status() == 0                      # every problem's status word, read and reset
     for b in range(bp.B):
         y = ys[b].cpu().numpy()
         assert oracle.max_stream_rel_l2(y, oracle.conv(ss[b], hs[b])) <= TOL, b

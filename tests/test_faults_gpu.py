@@ -126,13 +126,17 @@ def test_host_pipeline_allocation_failure(env):
     plan = Plan(65, 4, 512)
     plan.set_filters(torch.from_numpy(h).cuda())
     sh = torch.from_numpy(s).pin_memory()
+    plan.host_timing(True)
     env["OLS_FAIL_ALLOC"] = "2"          # the first chunk's output staging buffer
     with pytest.raises(_native.OLSError) as ei:
         plan.convolve_host(sh)
     assert ei.value.status == _native.OLS_ERR_ALLOC
+    # a failed call leaves no stage times behind
+    assert _native.ols_host_stage_ms(plan.handle)[0] == _native.OLS_ERR_NOT_READY
     env.pop("OLS_FAIL_ALLOC")
     y = plan.convolve_host(sh).numpy()
     assert oracle.max_stream_rel_l2(y, oracle.conv(s, h)) <= 2e-6
+    assert plan.host_stage_ms()["chunks"] == plan.last_launch_count() >= 1
     plan.close()
 
 

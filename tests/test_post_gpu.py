@@ -309,6 +309,11 @@ def test_peaks_capacity_and_arguments():
     assert f.size == 50 and np.all(may[f, j])
     st = torch.cuda.current_stream().cuda_stream
     sd = to_dev(s)
+    # count only: capacity 0, no record array
+    cnt2 = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    assert _native.ols_convolve_peaks(plan.handle, sd.data_ptr(), Ns, thr, None, 0, cnt2.data_ptr(), st) == 0
+    torch.cuda.synchronize()
+    assert int(cnt2.item()) == count
     assert _native.ols_convolve_peaks(plan.handle, sd.data_ptr(), Ns, thr, rec.data_ptr(), -1, cnt.data_ptr(),
                                       st) == _native.OLS_ERR_INVALID
     assert _native.ols_convolve_peaks(plan.handle, sd.data_ptr(), M - 1, thr, rec.data_ptr(), 5, cnt.data_ptr(),
