@@ -136,13 +136,41 @@ def all_reduce_sum(t: torch.Tensor, group=None) -> torch.Tensor:
     return out.to(t.device)
 
 
+def all_gather_candidates(rec: torch.Tensor, count: torch.Tensor, f0: int, group=None):
+    """Candidate records (ols_candidate: int64 j; int32 f; float power, as an
+    int64 tensor [capacity][2]) of every rank gathered on every rank, in rank
+    order, with this rank's filter offset f0 added to f.  count: the rank's
+    device count (may exceed its capacity; only stored records travel).
+    Returns (records [kept][2] int64 on rec's device, total count over ranks)."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    comm = rec.device if _device_collectives(group) else torch.device("cpu")
+    cap = rec.shape[0]
+    n_all = torch.tensor([int(count.item()), 0], dtype=torch.int64, device=comm)
+    n_all[1] = min(int(n_all[0].item()), cap)
+    sizes = [torch.empty_like(n_all) for _ in range(world)]
+    dist.all_gather(sizes, n_all, group=group)
+    kept = [int(t[1].item()) for t in sizes]
+    total = sum(int(t[0].item()) for t in sizes)
+    nmax = max(kept + [1])
+    words = rec[: kept[dist.get_rank(group)]].contiguous().view(torch.int32).view(-1, 4).clone()
+    words[:, 2] += f0                                          # the record's f, made global
+    buf = torch.zeros((nmax, 4), dtype=torch.int32, device=comm)
+    buf[: words.shape[0]] = words.to(comm)
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf, group=group)
+    whole = torch.cat([parts[r][: kept[r]] for r in range(world)], dim=0).contiguous()
+    return whole.view(torch.int64).view(-1, 2).to(rec.device), total
+
+
 class FilterSplit:
     """A bank of F filters of M taps split across the ranks of `group`: this
     rank owns filters [f0, f1) (``filter_range``) and convolves the whole
     signal with them on the current CUDA device through the library's
     kernels.  Segments and filters are independent (Sec. 3.2), so the forward
     pass needs no communication; ``convolve`` gathers the rows so every rank
-    gets y [F][Nout].  In the adjoint each rank's dh rows are final and ds is
+    gets y [F][Nout]; ``detect`` and ``peaks`` gather only the selected
+    candidates (Sec. 4.4).  In the adjoint each rank's dh rows are final and ds is
     the sum of every rank's contribution (one all-reduce of Ns samples).
     A rank without filters (F < world size) contributes zeros."""
 
@@ -180,6 +208,29 @@ class FilterSplit:
     def convolve(self, s: torch.Tensor) -> torch.Tensor:
         """y [F][Ns-M+1] on every rank: local rows, then one row gather."""
         return all_gather_rows(self.convolve_local(s), self.F, self.group)
+
+    def _select(self, mode: str, s: torch.Tensor, threshold: float, capacity: int):
+        if self.plan is None:
+            rec = torch.zeros((max(int(capacity), 1), 2), dtype=torch.int64, device=self.device)
+            cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        elif mode == "peaks":
+            rec, cnt = self.plan.convolve_peaks(s, threshold, capacity)
+        else:
+            rec, cnt = self.plan.convolve_detect(s, threshold, capacity)
+        return all_gather_candidates(rec, cnt, self.f0, self.group)
+
+    def detect(self, s: torch.Tensor, threshold: float, capacity: int):
+        """Candidates |y_f[j]|^2 >= threshold over the whole bank, on every rank:
+        each rank selects among its own filters (at most `capacity` records
+        each) and only the records travel.  Returns (records [n][2] int64 in
+        the ols_candidate layout with global f, see ``decode_candidates``;
+        total count over ranks, which exceeds n when a rank overflowed)."""
+        return self._select("detect", s, threshold, capacity)
+
+    def peaks(self, s: torch.Tensor, threshold: float, capacity: int):
+        """Peaks of the power over the whole bank (``Plan.convolve_peaks`` on
+        each rank's filters), gathered like ``detect``."""
+        return self._select("peaks", s, threshold, capacity)
 
     def convolve_backward(self, s: torch.Tensor, g: torch.Tensor, want_ds: bool = True, want_dh: bool = True):
         """g: the whole output gradient [F][Ns-M+1] (same on every rank).

@@ -148,3 +148,58 @@ def test_filter_ranges_tile_the_bank(F, world):
         assert 0 <= f0 <= f1 <= F
         seen[f0:f1] += 1
     assert np.all(seen == 1)
+
+
+def _records(j, f, p, cap):
+    rec = np.zeros(cap, dtype=[("j", "<i8"), ("f", "<i4"), ("power", "<f4")])
+    n = min(len(j), cap)
+    rec["j"][:n], rec["f"][:n], rec["power"][:n] = j[:n], f[:n], p[:n]
+    return torch.from_numpy(rec.view(np.int64).reshape(cap, 2).copy())
+
+
+def _cand_worker(rank, world, port, F, counts, cap, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    from paper_1910_01972_gb300 import decode_candidates
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        def local(r):
+            # rank r's candidates: local filter indices, found count counts[r] (may exceed cap)
+            f0, f1 = parallel.filter_range(F, world, r)
+            n = counts[r]
+            nf = max(f1 - f0, 1)
+            j = 1000 * r + np.arange(n, dtype=np.int64) * 7
+            fl = (np.arange(n) % nf).astype(np.int32)
+            p = (0.5 + r + np.arange(n) / 8).astype(np.float32)
+            return f0, j, fl, p
+        f0, j, fl, p = local(rank)
+        rec, total = parallel.all_gather_candidates(_records(j, fl, p, cap), torch.tensor([counts[rank]]), f0)
+        if rank == 0:
+            got = decode_candidates(rec, rec.shape[0])
+            want = [np.concatenate(a) for a in zip(*[
+                (fl_[:cap] + f0_, j_[:cap], p_[:cap]) for f0_, j_, fl_, p_ in (local(r) for r in range(world))])]
+            q.put((total, [a.tolist() for a in got], [a.tolist() for a in want]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("F,world,counts", [(5, 2, (3, 4)), (7, 3, (0, 9, 2)), (2, 3, (5, 6, 0)), (4, 2, (0, 0))])
+def test_candidates_gathered_with_global_filter_index(F, world, counts):
+    """Candidate records of each rank (its own filters, at most `cap` stored,
+    any count found) gathered in rank order on every rank, f made global, the
+    total count summed; a rank without filters or candidates contributes none."""
+    cap = 5
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_cand_worker, args=(r, world, port, F, counts, cap, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    for p in procs:
+        assert p.exitcode == 0, "rank failed"
+    total, got, want = q.get(timeout=5)
+    assert total == sum(counts)
+    assert got == want

@@ -7,7 +7,8 @@ the only exchanges (row gather, ds sum) go through host memory.  Blocks of
 uneven size and idle ranks (F < world size) included.  Rank 0 checks
 y, ds and dh against the FP64 oracle at the parity tolerances, and y and dh
 bit for bit against one unsplit plan (each filter's rows come from the same
-kernel arithmetic whichever plan holds the filter)."""
+kernel arithmetic whichever plan holds the filter); threshold and peak
+candidates gathered from the ranks equal the unsplit plan's exactly."""
 import os
 import socket
 
@@ -55,12 +56,26 @@ def _worker(rank, world, port, Ns, M, F, N, q):
         ds, dh = fs.convolve_backward(s, gy)
         torch.cuda.synchronize()
         launched = fs.plan.last_launch_count() if fs.plan is not None else 0
+        # candidate selection on each rank's filters, only the records gathered
+        p_all = (y.real ** 2 + y.imag ** 2)
+        thr = float(torch.quantile(p_all.flatten()[: 1 << 16], 0.99).item())
+        cand = {m: getattr(fs, m)(s, thr, 1 << 14) for m in ("detect", "peaks")}
+        torch.cuda.synchronize()
         fs.close()
         if rank == 0:
             whole = Plan(M, F, N)
             whole.set_filters(h)
             y1 = whole.convolve(s)
             ds1, dh1 = whole.convolve_backward(s, gy)
+            same_cand = True
+            from paper_1910_01972_gb300 import decode_candidates
+            for m, fn in (("detect", whole.convolve_detect), ("peaks", whole.convolve_peaks)):
+                rec1, cnt1 = fn(s, thr, 1 << 14)
+                torch.cuda.synchronize()
+                rec, total = cand[m]
+                a1 = set(zip(*[x.tolist() for x in decode_candidates(rec1, int(cnt1.item()))]))
+                a2 = set(zip(*[x.tolist() for x in decode_candidates(rec, rec.shape[0])]))
+                same_cand = same_cand and total == int(cnt1.item()) and a1 == a2 and len(a1) > 0
             torch.cuda.synchronize()
             whole.close()
             y_ref = oracle.conv(s_np, h_np)
@@ -70,7 +85,7 @@ def _worker(rank, world, port, Ns, M, F, N, q):
                    "dh_err": oracle.max_stream_rel_l2(dh.cpu().numpy(), dh_ref),
                    "y_bitwise": bool(torch.equal(y, y1)), "dh_bitwise": bool(torch.equal(dh, dh1)),
                    "ds_vs_whole": oracle.rel_l2(ds.cpu().numpy(), ds1.cpu().numpy().astype(np.complex128)),
-                   "launched": launched})
+                   "launched": launched, "same_candidates": same_cand})
     finally:
         dist.destroy_process_group()
 
@@ -93,4 +108,5 @@ def test_filter_split_ranks_run_the_kernels(F, world):
     assert r["y_bitwise"] and r["dh_bitwise"], r
     # ds: a sum over ranks in another order than the unsplit plan's; within rounding
     assert r["ds_vs_whole"] <= 1e-6, r
-    assert r["launched"] == 3                # rank 0's last library call: the adjoint's three kernels
+    assert r["launched"] == 3                # rank 0's adjoint call: its three kernels
+    assert r["same_candidates"], r           # detect and peaks over the split bank = the unsplit plan's
