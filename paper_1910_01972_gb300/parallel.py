@@ -5,7 +5,7 @@ outputs of one signal can be cut into contiguous ranges, one per rank; rank r
 computes y[:, j0:j1] from the input slice s[j0 : j1+M-1] (its outputs plus an
 M-1 sample halo) with no communication.  The adjoint needs two reductions:
 dh is a sum over ranks, and the input gradient of rank r's slice overlaps the
-next rank's by M-1 samples, which one point-to-point exchange adds.
+next rank's by M-1 samples, which a chain of point-to-point exchanges adds.
 
 The second way to split is along the filter bank: rank r convolves the whole
 signal with its own contiguous block of filters, so its outputs are whole
@@ -16,6 +16,10 @@ each rank's dh rows are final and the input gradient ds is a sum over ranks
 ``FilterSplit`` is that second split as a product call: each rank plans its
 own block of filters on its own device, runs the library's kernels for it,
 and the rows are gathered (forward) or ds is all-reduced (adjoint).
+``SignalSplit`` is the first: each rank plans the whole bank and runs the
+library's kernels on its own input slice; the output columns are gathered,
+and in the adjoint the slices' overlapping input gradients are added and dh
+is summed over ranks.
 
 Collectives use torch.distributed: NCCL on the ranks' CUDA tensors, any other
 backend (gloo) on host copies.
@@ -53,18 +57,21 @@ def input_range(Ns: int, M: int, world: int, rank: int):
 
 def reduce_input_gradient(ds_slice: torch.Tensor, M: int, world: int, rank: int, group=None) -> torch.Tensor:
     """ds_slice: the gradient w.r.t. this rank's input slice (length i1 - i0).
-    Sends its last M-1 entries to rank+1, adds the M-1 received from rank-1 to
-    its head, and returns the entries of input_range() (length b - a)."""
+    Adds the M-1 entries received from rank-1 to its head, then sends its last
+    M-1 entries -- received part included -- to rank+1, and returns the entries
+    of input_range() (length b - a).  The ranks form a chain: a range shorter
+    than M-1 has a head and a tail that overlap (an empty one, Nout < world,
+    is all overlap), and what such a rank received must travel on."""
     import torch.distributed as dist
     h = M - 1
     ds = ds_slice.clone()
     if h > 0 and world > 1:
-        if rank + 1 < world:
-            dist.send(ds[-h:].contiguous(), dst=rank + 1, group=group)
         if rank > 0:
             buf = torch.empty(h, dtype=ds.dtype, device=ds.device)
             dist.recv(buf, src=rank - 1, group=group)
             ds[:h] += buf
+        if rank + 1 < world:
+            dist.send(ds[-h:].contiguous(), dst=rank + 1, group=group)
     if rank + 1 < world and h > 0:
         return ds[:-h]
     return ds
@@ -251,4 +258,104 @@ class FilterSplit:
             if dh_loc is None:
                 dh_loc = torch.empty((self.f1 - self.f0, self.M), dtype=torch.complex64, device=self.device)
             dh = all_gather_rows(dh_loc, self.F, self.group)
+        return ds, dh
+
+
+# ------------------------------------------------------------ output-range split
+def _comm_device(t: torch.Tensor, group=None) -> torch.device:
+    return t.device if _device_collectives(group) else torch.device("cpu")
+
+
+def all_gather_pieces(local: torch.Tensor, sizes, dim: int, group=None) -> torch.Tensor:
+    """Every rank's piece of `local` along `dim` (rank r's is sizes[r] long)
+    concatenated in rank order on every rank, on `local`'s device.  Pieces are
+    padded to the largest for the collective."""
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    if local.shape[dim] != sizes[rank]:
+        raise ValueError("rank %d holds %d entries, expected %d" % (rank, local.shape[dim], sizes[rank]))
+    comm = _comm_device(local, group)
+    shape = list(local.shape)
+    shape[dim] = max(list(sizes) + [1])
+    buf = torch.zeros(shape, dtype=local.dtype, device=comm)
+    buf.narrow(dim, 0, sizes[rank]).copy_(local.to(comm))
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    if buf.is_complex():
+        dist.all_gather([torch.view_as_real(t) for t in parts], torch.view_as_real(buf), group=group)
+    else:
+        dist.all_gather(parts, buf, group=group)
+    whole = torch.cat([parts[r].narrow(dim, 0, sizes[r]) for r in range(world)], dim=dim)
+    return whole.to(local.device)
+
+
+class SignalSplit:
+    """One long signal split across the ranks of `group` by output range
+    (``shard``): rank r computes y[:, j0:j1] for the whole bank of F filters
+    from the input slice s[j0 : j1+M-1] with the library's kernels on the
+    current CUDA device -- no communication on the forward pass, since
+    segments are independent (Sec. 3.2).  ``convolve`` gathers the columns so
+    every rank gets y [F][Nout].  In the adjoint the gradients of two
+    neighbouring slices overlap by M-1 inputs (one send / receive adds them,
+    ``reduce_input_gradient``) and dh is summed over ranks.  A rank whose
+    output range is empty (Nout < world size) contributes nothing."""
+
+    def __init__(self, M: int, F: int, N: int = 0, group=None):
+        import torch.distributed as dist
+        from . import Plan
+        self.group = group
+        self.world, self.rank = dist.get_world_size(group), dist.get_rank(group)
+        self.M, self.F = int(M), int(F)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.plan = Plan(self.M, self.F, N)
+        self.N = self.plan.N
+
+    def close(self):
+        if self.plan is not None:
+            self.plan.close()
+            self.plan = None
+
+    def set_filters(self, h: torch.Tensor) -> None:
+        """h: the whole bank [F][M] complex64 (same on every rank)."""
+        self.plan.set_filters(h.to(self.device).contiguous())
+
+    def shard(self, Ns: int):
+        """(j0, j1, i0, i1) of this rank for a signal of Ns samples."""
+        return shard(Ns, self.M, self.world, self.rank)
+
+    def convolve_local(self, s: torch.Tensor) -> torch.Tensor:
+        """This rank's columns of y, [F][j1-j0], from the whole signal s (only
+        its slice is read)."""
+        j0, j1, i0, i1 = self.shard(s.shape[0])
+        if j1 == j0:
+            return torch.empty((self.F, 0), dtype=torch.complex64, device=self.device)
+        return self.plan.convolve(s[i0:i1])
+
+    def convolve(self, s: torch.Tensor) -> torch.Tensor:
+        """y [F][Ns-M+1] on every rank: local columns, then one column gather."""
+        Nout = s.shape[0] - self.M + 1
+        sizes = [b - a for a, b in (output_range(Nout, self.world, r) for r in range(self.world))]
+        return all_gather_pieces(self.convolve_local(s), sizes, 1, self.group)
+
+    def convolve_backward(self, s: torch.Tensor, g: torch.Tensor, want_ds: bool = True, want_dh: bool = True):
+        """g: the whole output gradient [F][Ns-M+1] (same on every rank; only
+        this rank's columns are read).  Returns (ds [Ns], dh [F][M]) on every
+        rank, each None if not wanted."""
+        Ns = s.shape[0]
+        if tuple(g.shape) != (self.F, Ns - self.M + 1):
+            raise ValueError("g must have shape [F][Ns-M+1]")
+        j0, j1, i0, i1 = self.shard(Ns)
+        ds_loc = torch.zeros(i1 - i0, dtype=torch.complex64, device=self.device)
+        dh_loc = torch.zeros((self.F, self.M), dtype=torch.complex64, device=self.device)
+        if j1 > j0:
+            a, b = self.plan.convolve_backward(s[i0:i1], g[:, j0:j1].contiguous(), want_ds, want_dh)
+            ds_loc = a if a is not None else ds_loc
+            dh_loc = b if b is not None else dh_loc
+        ds = dh = None
+        if want_ds:
+            comm = _comm_device(ds_loc, self.group)
+            mine = reduce_input_gradient(ds_loc.to(comm), self.M, self.world, self.rank, self.group)
+            sizes = [b - a for a, b in (input_range(Ns, self.M, self.world, r) for r in range(self.world))]
+            ds = all_gather_pieces(mine.to(self.device), sizes, 0, self.group)
+        if want_dh:
+            dh = all_reduce_sum(dh_loc, self.group)
         return ds, dh

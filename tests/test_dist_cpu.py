@@ -46,11 +46,15 @@ def _worker(rank, world, port, Ns, M, F, q):
         gy = g.normal(size=(F, Ns - M + 1)) + 1j * g.normal(size=(F, Ns - M + 1))
         j0, j1, i0, i1 = parallel.shard(Ns, M, world, rank)
         # forward: each rank convolves its slice, no communication
-        y_loc = torch.from_numpy(oracle.conv(s[i0:i1], h))
+        empty = j1 == j0                      # Nout < world: a rank without outputs
+        y_loc = torch.from_numpy(np.zeros((F, 0), np.complex128) if empty else oracle.conv(s[i0:i1], h))
         parts = [None] * world
         dist.all_gather_object(parts, (j0, y_loc.numpy()))
         # adjoint on the slice, then the two reductions
-        ds_loc, dh_loc = oracle.adjoint(s[i0:i1], h, gy[:, j0:j1])
+        if empty:
+            ds_loc, dh_loc = np.zeros(i1 - i0, np.complex128), np.zeros((F, M), np.complex128)
+        else:
+            ds_loc, dh_loc = oracle.adjoint(s[i0:i1], h, gy[:, j0:j1])
         ds_mine = parallel.reduce_input_gradient(torch.from_numpy(ds_loc), M, world, rank)
         dh_all = parallel.reduce_filter_gradient(torch.from_numpy(dh_loc))
         ds_parts = [None] * world
@@ -69,12 +73,16 @@ def _worker(rank, world, port, Ns, M, F, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2])
-def test_two_rank_split_equals_whole_signal(world):
+@pytest.mark.parametrize("Ns,M,world", [(3000, 65, 2), (100, 40, 7), (41, 40, 3), (500, 1, 3)])
+def test_two_rank_split_equals_whole_signal(Ns, M, world):
+    """Output-range split: outputs concatenated, input gradients of neighbouring
+    slices added, dh summed.  Ranges shorter than M-1 (a slice's head and tail
+    overlap, so a rank must pass on what it received) and an empty range
+    (Nout < world) included."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    Ns, M, F = 3000, 65, 3
+    F = 3
     procs = [ctx.Process(target=_worker, args=(r, world, port, Ns, M, F, q)) for r in range(world)]
     for p in procs:
         p.start()

@@ -110,3 +110,57 @@ def test_filter_split_ranks_run_the_kernels(F, world):
     assert r["ds_vs_whole"] <= 1e-6, r
     assert r["launched"] == 3                # rank 0's adjoint call: its three kernels
     assert r["same_candidates"], r           # detect and peaks over the split bank = the unsplit plan's
+
+
+def _signal_worker(rank, world, port, Ns, M, F, N, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    import oracle
+    import synth
+    from paper_1910_01972_gb300 import parallel
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g = np.random.Generator(np.random.PCG64(800 + Ns + world))
+        s_np, h_np = synth.signal(g, Ns), synth.filters(g, F, M)
+        gy_np = (g.normal(size=(F, Ns - M + 1)) + 1j * g.normal(size=(F, Ns - M + 1))).astype(np.complex64)
+        s, h, gy = (torch.from_numpy(a).cuda() for a in (s_np, h_np, gy_np))
+        sp = parallel.SignalSplit(M, F, N)
+        sp.set_filters(h)
+        y = sp.convolve(s)
+        ds, dh = sp.convolve_backward(s, gy)
+        torch.cuda.synchronize()
+        sp.close()
+        if rank == 0:
+            y_ref = oracle.conv(s_np, h_np)
+            ds_ref, dh_ref = oracle.adjoint(s_np, h_np, gy_np)
+            q.put({"y_err": oracle.max_stream_rel_l2(y.cpu().numpy(), y_ref,
+                                                     oracle.stream_scale(s_np, h_np, y_ref.shape[1])),
+                   "ds_err": oracle.rel_l2(ds.cpu().numpy(), ds_ref),
+                   "dh_err": oracle.max_stream_rel_l2(dh.cpu().numpy(), dh_ref),
+                   "shapes": (tuple(y.shape), tuple(ds.shape), tuple(dh.shape))})
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("Ns,M,F,N,world", [(50_000, 129, 5, 1024, 2), (50_000, 129, 3, 1024, 3),
+                                            (300, 129, 2, 512, 3), (130, 129, 2, 256, 3)])
+def test_signal_split_ranks_run_the_kernels(Ns, M, F, N, world):
+    """The output-range split (parallel.SignalSplit): each rank convolves its
+    input slice with the whole bank through the library's kernels; columns
+    gathered, neighbouring slices' input gradients added, dh summed.  Ranges
+    shorter than M-1 and an empty range (Nout = 2 over 3 ranks) included."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_signal_worker, args=(r, world, port, Ns, M, F, N, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    for p in procs:
+        assert p.exitcode == 0, "rank failed"
+    r = q.get(timeout=5)
+    assert r["shapes"] == ((F, Ns - M + 1), (Ns,), (F, M)), r
+    assert r["y_err"] <= TOL and r["ds_err"] <= TOL_DS and r["dh_err"] <= TOL_DH, r
