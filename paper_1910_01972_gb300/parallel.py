@@ -143,24 +143,28 @@ def all_reduce_sum(t: torch.Tensor, group=None) -> torch.Tensor:
     return out.to(t.device)
 
 
-def all_gather_candidates(rec: torch.Tensor, count: torch.Tensor, f0: int, group=None):
+def all_gather_candidates(rec: torch.Tensor, count, f0: int = 0, group=None, j_shift: int = 0):
     """Candidate records (ols_candidate: int64 j; int32 f; float power, as an
     int64 tensor [capacity][2]) of every rank gathered on every rank, in rank
-    order, with this rank's filter offset f0 added to f.  count: the rank's
-    device count (may exceed its capacity; only stored records travel).
-    Returns (records [kept][2] int64 on rec's device, total count over ranks)."""
+    order, with this rank's filter offset f0 added to f and j_shift to j.
+    count: the rank's count (a device tensor or an int; may exceed the
+    capacity: only stored records travel).  Returns (records [kept][2] int64
+    on rec's device, total count over ranks)."""
     import torch.distributed as dist
     world = dist.get_world_size(group)
     comm = rec.device if _device_collectives(group) else torch.device("cpu")
     cap = rec.shape[0]
-    n_all = torch.tensor([int(count.item()), 0], dtype=torch.int64, device=comm)
+    n_all = torch.tensor([int(count.item()) if torch.is_tensor(count) else int(count), 0], dtype=torch.int64,
+                         device=comm)
     n_all[1] = min(int(n_all[0].item()), cap)
     sizes = [torch.empty_like(n_all) for _ in range(world)]
     dist.all_gather(sizes, n_all, group=group)
     kept = [int(t[1].item()) for t in sizes]
     total = sum(int(t[0].item()) for t in sizes)
     nmax = max(kept + [1])
-    words = rec[: kept[dist.get_rank(group)]].contiguous().view(torch.int32).view(-1, 4).clone()
+    mine = rec[: kept[dist.get_rank(group)]].clone()
+    mine[:, 0] += j_shift                                      # the record's j, made global
+    words = mine.view(torch.int32).view(-1, 4)
     words[:, 2] += f0                                          # the record's f, made global
     buf = torch.zeros((nmax, 4), dtype=torch.int32, device=comm)
     buf[: words.shape[0]] = words.to(comm)
@@ -335,6 +339,41 @@ class SignalSplit:
         Nout = s.shape[0] - self.M + 1
         sizes = [b - a for a, b in (output_range(Nout, self.world, r) for r in range(self.world))]
         return all_gather_pieces(self.convolve_local(s), sizes, 1, self.group)
+
+    def _select(self, mode: str, s: torch.Tensor, threshold: float, capacity: int):
+        Ns = s.shape[0]
+        Nout = Ns - self.M + 1
+        j0, j1, _, _ = self.shard(Ns)
+        if j1 == j0:
+            return all_gather_candidates(torch.zeros((0, 2), dtype=torch.int64, device=self.device), 0, 0,
+                                         self.group)
+        # peaks look at j - 1 and j + 1: the slice is widened by one output on each side
+        # that has a neighbouring range, and only this rank's outputs are kept
+        a = j0 - 1 if (mode == "peaks" and j0 > 0) else j0
+        b = j1 + 1 if (mode == "peaks" and j1 < Nout) else j1
+        fn = self.plan.convolve_peaks if mode == "peaks" else self.plan.convolve_detect
+        rec, cnt = fn(s[a:b + self.M - 1], threshold, capacity)
+        count = int(cnt.item())
+        stored = rec[: min(count, rec.shape[0])]
+        keep = stored[(stored[:, 0] >= j0 - a) & (stored[:, 0] < j1 - a)]
+        # past the capacity the total is what the kernel found (the one-output widening included)
+        total = keep.shape[0] if count <= rec.shape[0] else count
+        return all_gather_candidates(keep, total, 0, self.group, a)
+
+    def detect(self, s: torch.Tensor, threshold: float, capacity: int):
+        """Candidates |y_f[j]|^2 >= threshold over the whole signal, on every
+        rank: each rank selects in its own output range, only the records
+        travel (j made global).  Returns (records, total) like
+        ``FilterSplit.detect``; a rank past its capacity counts what its
+        kernel found."""
+        return self._select("detect", s, threshold, capacity)
+
+    def peaks(self, s: torch.Tensor, threshold: float, capacity: int):
+        """Peaks of the power over the whole signal: each rank's slice is
+        widened by one output towards each neighbouring range so that the
+        outputs at its range's ends see both neighbours; the two ends of the
+        whole stream keep their one-sided rule.  Gathered like ``detect``."""
+        return self._select("peaks", s, threshold, capacity)
 
     def convolve_backward(self, s: torch.Tensor, g: torch.Tensor, want_ds: bool = True, want_dh: bool = True):
         """g: the whole output gradient [F][Ns-M+1] (same on every rank; only

@@ -182,11 +182,13 @@ def _cand_worker(rank, world, port, F, counts, cap, q):
             p = (0.5 + r + np.arange(n) / 8).astype(np.float32)
             return f0, j, fl, p
         f0, j, fl, p = local(rank)
-        rec, total = parallel.all_gather_candidates(_records(j, fl, p, cap), torch.tensor([counts[rank]]), f0)
+        rec, total = parallel.all_gather_candidates(_records(j, fl, p, cap), torch.tensor([counts[rank]]), f0,
+                                                    j_shift=100_000 * rank)
         if rank == 0:
             got = decode_candidates(rec, rec.shape[0])
             want = [np.concatenate(a) for a in zip(*[
-                (fl_[:cap] + f0_, j_[:cap], p_[:cap]) for f0_, j_, fl_, p_ in (local(r) for r in range(world))])]
+                (fl_[:cap] + f0_, j_[:cap] + 100_000 * r, p_[:cap])
+                for r, (f0_, j_, fl_, p_) in enumerate(local(r) for r in range(world))])]
             q.put((total, [a.tolist() for a in got], [a.tolist() for a in want]))
     finally:
         dist.destroy_process_group()

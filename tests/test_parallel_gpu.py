@@ -130,8 +130,31 @@ def _signal_worker(rank, world, port, Ns, M, F, N, q):
         sp.set_filters(h)
         y = sp.convolve(s)
         ds, dh = sp.convolve_backward(s, gy)
+        pw = (y.real ** 2 + y.imag ** 2).double().cpu().numpy()
+        thr = float(np.quantile(pw, 0.95))
+        cand = {m: getattr(sp, m)(s, thr, 1 << 14) for m in ("detect", "peaks")}
         torch.cuda.synchronize()
         sp.close()
+        if rank == 0:
+            import oracle as orc
+            from paper_1910_01972_gb300 import decode_candidates
+            p_ref = orc.power(s_np, h_np)
+            band = 2e-5
+            inf = float("inf")
+            left = np.pad(p_ref[:, :-1], ((0, 0), (1, 0)), constant_values=-inf)
+            right = np.pad(p_ref[:, 1:], ((0, 0), (0, 1)), constant_values=-inf)
+            sets_ok = True
+            for m, (must, may) in {
+                    "detect": (p_ref >= thr * (1 + band), p_ref >= thr * (1 - band)),
+                    "peaks": ((p_ref >= thr * (1 + band)) & (p_ref > left * (1 + band)) & (p_ref >= right * (1 + band)),
+                              (p_ref >= thr * (1 - band)) & (p_ref >= left * (1 - band)) & (p_ref >= right * (1 - band)))
+            }.items():
+                rec, total = cand[m]
+                f_, j_, _ = decode_candidates(rec, rec.shape[0])
+                got = set(zip(f_.tolist(), j_.tolist()))
+                must_s = set(zip(*[x.tolist() for x in np.nonzero(must)]))
+                may_s = set(zip(*[x.tolist() for x in np.nonzero(may)]))
+                sets_ok = sets_ok and total == len(got) == rec.shape[0] and must_s <= got <= may_s
         if rank == 0:
             y_ref = oracle.conv(s_np, h_np)
             ds_ref, dh_ref = oracle.adjoint(s_np, h_np, gy_np)
@@ -139,7 +162,7 @@ def _signal_worker(rank, world, port, Ns, M, F, N, q):
                                                      oracle.stream_scale(s_np, h_np, y_ref.shape[1])),
                    "ds_err": oracle.rel_l2(ds.cpu().numpy(), ds_ref),
                    "dh_err": oracle.max_stream_rel_l2(dh.cpu().numpy(), dh_ref),
-                   "shapes": (tuple(y.shape), tuple(ds.shape), tuple(dh.shape))})
+                   "shapes": (tuple(y.shape), tuple(ds.shape), tuple(dh.shape)), "candidates": sets_ok})
     finally:
         dist.destroy_process_group()
 
@@ -149,8 +172,10 @@ def _signal_worker(rank, world, port, Ns, M, F, N, q):
 def test_signal_split_ranks_run_the_kernels(Ns, M, F, N, world):
     """The output-range split (parallel.SignalSplit): each rank convolves its
     input slice with the whole bank through the library's kernels; columns
-    gathered, neighbouring slices' input gradients added, dh summed.  Ranges
-    shorter than M-1 and an empty range (Nout = 2 over 3 ranks) included."""
+    gathered, neighbouring slices' input gradients added, dh summed; threshold
+    and peak candidates selected per range (peaks on a slice widened by one
+    output each side) and gathered.  Ranges shorter than M-1 and an empty
+    range (Nout = 2 over 3 ranks) included."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -164,3 +189,4 @@ def test_signal_split_ranks_run_the_kernels(Ns, M, F, N, world):
     r = q.get(timeout=5)
     assert r["shapes"] == ((F, Ns - M + 1), (Ns,), (F, M)), r
     assert r["y_err"] <= TOL and r["ds_err"] <= TOL_DS and r["dh_err"] <= TOL_DH, r
+    assert r["candidates"], r            # threshold and peak candidates over the split = the oracle's rule
