@@ -1,6 +1,6 @@
 """Maximum sizes: a signal of more than 2^31 samples (outputs past the 32-bit
 index range) through the fused complex kernel, the real-to-real kernel, the
-post-processing kernels, the tensor-core kernel (FP32 and split-plane input)
+post-processing kernels (power, derivative, threshold and peak candidates), the tensor-core kernel (FP32 and split-plane input)
 and the adjoint, checked at sampled outputs against the FP64 oracle
 (tolerance 2e-6 relative L2, the FP32 bar; the tensor-core form's FP16 bound
 is the same).  The signal is drawn on the device (17 GB complex, 8.6 GB
@@ -223,4 +223,54 @@ def test_adjoint_beyond_2_to_31():
     assert oracle.max_stream_rel_l2(dh.cpu().numpy(), dh_ref) <= 1e-5
     plan.close()
     del ds, s
+    torch.cuda.empty_cache()
+
+
+def test_detect_and_peaks_beyond_2_to_31():
+    """Threshold and peak candidates past index 2^31.  Detection runs the power
+    kernel's segments, so its candidates are exactly the (0, j) with p[j] >=
+    threshold in the power kernel's output (same FP32 values); peaks run the
+    derivative's L-2 segments and are bracketed by the peak rule on that
+    power with a relative margin of 2e-5 on every comparison."""
+    M, F, N = 64, 1, 512
+    g = np.random.Generator(np.random.PCG64(80))
+    h = synth.filters(g, F, M)
+    s = synth.device_signal(NS, seed=504)
+    plan = Plan(M, F, N)
+    plan.set_filters(torch.from_numpy(h).cuda())
+    p = plan.convolve_power(s)[0]
+    thr = float(torch.quantile(p[:: 1 << 10].float(), 0.9999).item())
+    above = p >= thr
+    n_above = int(above.sum().item())
+    cap = n_above + 1024
+    rec, cnt = plan.convolve_detect(s, thr, cap)
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == n_above
+    j = rec[:n_above, 0]
+    seen = torch.zeros_like(above)
+    seen[j] = True
+    assert int(seen.sum().item()) == n_above and torch.equal(seen, above)   # masks: no index list of 2^31+
+    assert int(j.max().item()) > (1 << 31)
+    del above, seen
+    band = 2e-5
+    left = torch.cat([torch.full((1,), -float("inf"), device=p.device), p[:-1]])
+    must = (p >= thr * (1 + band)) & (p > left * (1 + band))
+    may = (p >= thr * (1 - band)) & (p >= left * (1 - band))
+    del left
+    right = torch.cat([p[1:], torch.full((1,), -float("inf"), device=p.device)])
+    must &= p >= right * (1 + band)
+    may &= p >= right * (1 - band)
+    del right
+    rec, cnt = plan.convolve_peaks(s, thr, cap)
+    torch.cuda.synchronize()
+    n = int(cnt.item())
+    jp = rec[:n, 0]
+    assert int(must.sum().item()) <= n <= int(may.sum().item())
+    assert bool(may[jp].all())
+    got = torch.zeros_like(must)
+    got[jp] = True
+    assert bool((got | ~must).all()) and int(got.sum().item()) == n
+    assert int(jp.max().item()) > (1 << 31)
+    plan.close()
+    del s, p, must, may, got
     torch.cuda.empty_cache()
