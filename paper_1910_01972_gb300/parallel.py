@@ -66,12 +66,14 @@ def reduce_input_gradient(ds_slice: torch.Tensor, M: int, world: int, rank: int,
     h = M - 1
     ds = ds_slice.clone()
     if h > 0 and world > 1:
+        def real(t):      # complex values travel as (re, im) pairs
+            return torch.view_as_real(t) if t.is_complex() else t
         if rank > 0:
             buf = torch.empty(h, dtype=ds.dtype, device=ds.device)
-            dist.recv(buf, src=rank - 1, group=group)
+            dist.recv(real(buf), src=rank - 1, group=group)
             ds[:h] += buf
         if rank + 1 < world:
-            dist.send(ds[-h:].contiguous(), dst=rank + 1, group=group)
+            dist.send(real(ds[-h:].contiguous()), dst=rank + 1, group=group)
     if rank + 1 < world and h > 0:
         return ds[:-h]
     return ds
