@@ -3,7 +3,7 @@
 // "optional post-processing" step; Sec. 4.3: per-element and non-local
 // post-processing; Sec. 4.4: reducing the output before it leaves the GPU).
 //
-// Three epilogues on the same segment body as ols_forward.cu (segment FFT
+// Four epilogues on the same segment body as ols_forward.cu (segment FFT
 // kept in registers for all filters; per filter the point-wise product, the
 // inverse FFT and the discard of aliased samples):
 // * POWER   (per element)   p_f[j] = |y_f[j]|^2, written as FP32 (half the
